@@ -1,0 +1,211 @@
+/*
+ * hm.h -- C ABI of libhm: the product Y = A X of a HODLR or HSS matrix A with
+ * a block X of r vectors on one GB300 (sm_103a).
+ *
+ * Method: the fast products of Sec. 4.1 and Fig. 4.1 of "hm-toolbox: Matlab
+ * software for HODLR and HSS matrices" (Massei, Robol, Kressner).  HODLR
+ * (Def. 2.2): dense leaf blocks plus, on every level, sibling blocks U V^T.
+ * HSS (Def. 2.3, Eq. 2.2): leaf bases, nested translation operators R_U,
+ * R_V and core blocks S (B12, B21 in the paper's class).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an hm_status.  Nothing aborts, nothing prints.
+ *    Invalid shapes and pointers are rejected with HM_EINVAL before any work
+ *    is queued.  hm_last_error() gives a one-line description of the last
+ *    failure on the calling thread.
+ *  - Indices are 0-based; blocks passed in are float64, column-major
+ *    (Matlab layout), leading dimension = number of rows.
+ *  - Node ids are level order: level l (root = 0), position j has id
+ *    2^l - 1 + j.  Internal nodes are ids 0..L-2, leaves L-1..2L-2, with
+ *    L = 2^p leaves.
+ *  - Objects are created by *_create and released by hm_destroy (NULL-safe).
+ *    An object may be used from several host threads only if the caller
+ *    serialises calls on it, except where a function says otherwise.
+ *  - Streams are cudaStream_t values passed as void* (NULL = legacy default
+ *    stream).  All GPU work of a call is queued on that stream and is
+ *    asynchronous unless stated.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HM_OK = 0,
+  HM_EINVAL = 1,        /* bad argument, shape, pointer or handle */
+  HM_ENOMEM = 2,        /* device or host allocation failed, or budget exceeded */
+  HM_EBUSY = 3,         /* admission refused (no free slot); retry later */
+  HM_ETIMEOUT = 4,      /* a bounded wait ran out (host wait or device barrier) */
+  HM_ECUDA = 5,         /* a CUDA runtime call failed */
+  HM_EUNSUPPORTED = 6   /* valid request outside this library's scope */
+} hm_status;
+
+/* Storage / input-output element types.
+ * HM_BF16X2 stores every generator entry a as a pair hi = RN_bf16(a),
+ * lo = RN_bf16(a - hi); the tensor-core product is hi*xhi + hi*xlo + lo*xhi. */
+typedef enum { HM_F64 = 0, HM_F32 = 1, HM_BF16 = 2, HM_BF16X2 = 3 } hm_dtype;
+
+typedef enum { HM_HODLR = 0, HM_HSS = 1 } hm_kind;
+
+typedef struct hm_tree hm_tree;
+typedef struct hm_matrix hm_matrix;
+typedef struct hm_batch hm_batch;
+typedef struct hm_server hm_server;
+
+/* Static description of a status code; never NULL. */
+const char* hm_status_string(hm_status s);
+/* Detail of the last failed call on this host thread; never NULL. */
+const char* hm_last_error(void);
+/* Library version string, e.g. "hm 1.0 sm_103a". */
+const char* hm_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* Cluster trees (Def. 2.1; vector form of Sec. 3.7; default split Sec. 3.1) */
+/* ---------------------------------------------------------------------- */
+
+/* Tree from the leaf-end vector c = [n_1, ..., n_L] (Sec. 3.7): leaf i holds
+ * rows c[i-1] .. c[i]-1 (c[-1] = 0).  num_leaves must be a power of two,
+ * c non-decreasing, c[L-1] = n.  Empty leaves are allowed (Def. 2.1). */
+hm_status hm_tree_create(int64_t n, const int64_t* leaf_ends, int32_t num_leaves, hm_tree** out);
+
+/* Default tree of Sec. 3.1: {1..n} splits into {1..ceil(n/2)} and the rest;
+ * every node of a level splits while some node of the level exceeds n_min. */
+hm_status hm_tree_default(int64_t n, int64_t n_min, hm_tree** out);
+
+/* n, depth p and number of leaves 2^p of a tree (any pointer may be NULL). */
+hm_status hm_tree_shape(const hm_tree* t, int64_t* n, int32_t* depth, int32_t* num_leaves);
+
+/* Copies the leaf-end vector (num_leaves entries) into leaf_ends. */
+hm_status hm_tree_leaf_ends(const hm_tree* t, int64_t* leaf_ends);
+
+/* ---------------------------------------------------------------------- */
+/* Generators                                                              */
+/* ---------------------------------------------------------------------- */
+
+/* HODLR generators, the hodlr class of Sec. 2.1 flattened in node order.
+ * For internal node q with children a (left) and b (right):
+ *   A(I_a, I_b) = U12[q] * V12[q]^T,  U12[q]: |I_a| x k12[q], V12[q]: |I_b| x k12[q]
+ *   A(I_b, I_a) = U21[q] * V21[q]^T,  U21[q]: |I_b| x k21[q], V21[q]: |I_a| x k21[q]
+ * D[i] is the m_i x m_i diagonal block of leaf i.  Pointers may be host or
+ * device memory (unified addressing); a pointer to an empty block may be NULL.
+ * Arrays D has L entries; U12, V12, U21, V21, k12, k21 have L-1 entries. */
+typedef struct {
+  const double* const* D;
+  const double* const* U12;
+  const double* const* V12;
+  const double* const* U21;
+  const double* const* V21;
+  const int32_t* k12;
+  const int32_t* k21;
+} hm_hodlr_gens;
+
+/* HSS generators, the hss class of Sec. 2.2 flattened in node order.
+ * ku[q], kv[q]: ranks of the row basis U_q and the column basis V_q of node q
+ * (2L-1 entries; the root's are ignored).  Leaf i (node L-1+i):
+ *   D[i]: m_i x m_i, U[i]: m_i x ku, V[i]: m_i x kv.
+ * Internal non-root node q with children a, b (Eq. 2.2):
+ *   RU[q] = [Rl; Rr]: (ku[a] + ku[b]) x ku[q],  RV[q] = [Wl; Wr]: (kv[a] + kv[b]) x kv[q]
+ *   (arrays of 2L-1 entries indexed by node id; other entries ignored).
+ * Internal node q (root included), core blocks of its children:
+ *   B12[q]: ku[a] x kv[b] so that A(I_a, I_b) = U_a B12[q] V_b^T,
+ *   B21[q]: ku[b] x kv[a] so that A(I_b, I_a) = U_b B21[q] V_a^T  (L-1 entries). */
+typedef struct {
+  const double* const* D;
+  const double* const* U;
+  const double* const* V;
+  const double* const* RU;
+  const double* const* RV;
+  const double* const* B12;
+  const double* const* B21;
+  const int32_t* ku;
+  const int32_t* kv;
+} hm_hss_gens;
+
+/* ---------------------------------------------------------------------- */
+/* Matrices                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Creates a HODLR matrix (Def. 2.2) on the current CUDA device.  The
+ * generators are copied, converted to `storage` (round to nearest even) and
+ * packed into library-owned device memory; the caller may free its buffers
+ * when the call returns.  Ranks are padded with zero columns to the largest
+ * rank of each level; the padded product is exact.  Synchronous. */
+hm_status hm_hodlr_create(const hm_tree* t, const hm_hodlr_gens* g, hm_dtype storage, hm_matrix** out);
+
+/* Creates an HSS matrix (Def. 2.3 with Eq. 2.2) on the current device; same
+ * ownership and padding rules as hm_hodlr_create.  Translation and coupling
+ * operators are held in float64 for HM_F64 storage and in float32 otherwise. */
+hm_status hm_hss_create(const hm_tree* t, const hm_hss_gens* g, hm_dtype storage, hm_matrix** out);
+
+typedef struct {
+  int32_t kind;          /* hm_kind */
+  int32_t storage;       /* hm_dtype */
+  int64_t n;
+  int32_t depth;         /* p */
+  int32_t num_leaves;    /* 2^p */
+  int32_t leaf_pad;      /* padded leaf width used by the kernels */
+  int32_t rank_total;    /* HODLR: sum over levels of the padded ranks; HSS: padded rank */
+  int64_t generator_elements;  /* unpadded count: HODLR n m + 2 n k p; HSS as Sec. 2.2 */
+  size_t  generator_bytes;     /* algorithmic bytes of the generators in `storage` */
+  size_t  device_bytes;        /* bytes the library holds on the device for A */
+} hm_matrix_info_t;
+
+hm_status hm_matrix_info(const hm_matrix* A, hm_matrix_info_t* out);
+
+/* Algorithmic generator bytes (the figure a roofline divides by time). */
+hm_status hm_matrix_bytes(const hm_matrix* A, size_t* bytes);
+
+/* Reserves device scratch for products with up to r_max right-hand sides so
+ * that later calls allocate nothing (needed before CUDA-graph capture).
+ * Synchronous. */
+hm_status hm_matrix_reserve(hm_matrix* A, int64_t r_max);
+
+/* ---------------------------------------------------------------------- */
+/* Products                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Y = A X (overwrite) for a HODLR matrix: dense leaf blocks times X plus, on
+ * every level, each sibling block's U (V^T X) (Sec. 4.1; Fig. 4.1, left).
+ *   X: n x r, column-major, leading dimension ldx >= max(n, 1), type xt
+ *      (HM_F64, HM_F32 or HM_BF16); Y: n x r, ldy >= max(n, 1), type yt
+ *      (HM_F64 or HM_F32).  HM_F64 storage requires xt = yt = HM_F64.
+ *   X and Y may be device pointers (used asynchronously on `stream`) or host
+ *   pointers (then the call stages them through device scratch and returns
+ *   after Y has been written back).  X and Y must not overlap.
+ *   r = 0 or n = 0 is a no-op.  Calls on the same matrix must not run
+ *   concurrently on different streams: they share the matrix's scratch.
+ * Results are deterministic: the reduction order does not depend on timing
+ * or on other work on the device. */
+hm_status hm_hodlr_matmat(const hm_matrix* A, int64_t r, const void* X, int64_t ldx, hm_dtype xt,
+                          void* Y, int64_t ldy, hm_dtype yt, void* stream);
+
+/* Y = A X for an HSS matrix (Sec. 4.1; Fig. 4.1, right): leaf V^T X, upsweep
+ * through R_V, couplings S on levels 1..p, downsweep through R_U, leaf U plus
+ * D X.  Arguments and rules as hm_hodlr_matmat. */
+hm_status hm_hss_matmat(const hm_matrix* A, int64_t r, const void* X, int64_t ldx, hm_dtype xt,
+                        void* Y, int64_t ldy, hm_dtype yt, void* stream);
+
+/* Waits for `stream` and reports whether a device-side bounded wait of this
+ * library timed out since the last call (HM_ETIMEOUT), then clears the flag. */
+hm_status hm_device_status(void* stream);
+
+/* Selects the kernel family for later products on this matrix:
+ * 0 = automatic (tensor cores when r is wide enough and storage is BF16 or
+ * BF16X2), 1 = SIMT only, 2 = tensor cores whenever supported. */
+hm_status hm_matrix_set_path(hm_matrix* A, int32_t path);
+
+/* Releases any object created by this library (tree, matrix, batch, server).
+ * NULL-safe.  A matrix registered with a server must be released after the
+ * server. */
+void hm_destroy(void* any);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H */

@@ -1,0 +1,12 @@
+"""GB300-native HODLR/HSS matrix-times-block products (sm_103a CUDA kernels).
+
+Python binding of libhm (include/hm.h).  The library must be built first
+(``paper_1909_07909_gb300.build.build()``); importing without it raises.
+"""
+
+from ._lib import (HM_BF16, HM_BF16X2, HM_F32, HM_F64, HM_HODLR, HM_HSS, HMError,  # noqa: F401
+                   LIB_PATH, lib)
+from .api import Matrix, Tree, colmajor, device_status  # noqa: F401
+
+__all__ = ["Tree", "Matrix", "colmajor", "device_status", "HMError", "lib", "LIB_PATH",
+           "HM_F64", "HM_F32", "HM_BF16", "HM_BF16X2", "HM_HODLR", "HM_HSS"]

@@ -1,0 +1,220 @@
+"""Python objects over the C ABI: trees, HODLR/HSS matrices and their products.
+
+Only argument marshalling happens here; every step of a product runs in the
+library's CUDA kernels.  Blocks are passed as float64 column-major numpy
+arrays; right-hand sides are (n, r) column-major torch tensors (device or
+host) or Fortran-ordered numpy arrays (host).
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import check, lib
+
+vp = C.c_void_p
+
+try:  # torch is only needed for device tensors
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+
+def _dtype_code(d):
+    if isinstance(d, int):
+        return d
+    if isinstance(d, str):
+        return L.DTYPES[d]
+    if torch is not None:
+        if d == torch.float64:
+            return L.HM_F64
+        if d == torch.float32:
+            return L.HM_F32
+        if d == torch.bfloat16:
+            return L.HM_BF16
+    if d == np.float64:
+        return L.HM_F64
+    if d == np.float32:
+        return L.HM_F32
+    raise ValueError("unsupported dtype %r" % (d,))
+
+
+class Tree:
+    """Cluster tree (Def. 2.1) given by its leaf-end vector c (Sec. 3.7)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @classmethod
+    def from_leaf_ends(cls, c):
+        c = [int(v) for v in c]
+        arr = (C.c_int64 * len(c))(*c)
+        h = vp()
+        check(lib.hm_tree_create(c[-1] if c else 0, arr, len(c), C.byref(h)), "hm_tree_create")
+        return cls(h)
+
+    @classmethod
+    def default(cls, n, n_min=256):
+        h = vp()
+        check(lib.hm_tree_default(int(n), int(n_min), C.byref(h)), "hm_tree_default")
+        return cls(h)
+
+    def shape(self):
+        n, p, L_ = C.c_int64(), C.c_int32(), C.c_int32()
+        check(lib.hm_tree_shape(self._h, C.byref(n), C.byref(p), C.byref(L_)), "hm_tree_shape")
+        return n.value, p.value, L_.value
+
+    @property
+    def leaf_ends(self):
+        _, _, L_ = self.shape()
+        arr = (C.c_int64 * L_)()
+        check(lib.hm_tree_leaf_ends(self._h, arr), "hm_tree_leaf_ends")
+        return [int(v) for v in arr]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.hm_destroy(h)
+            self._h = None
+
+
+def _ptrs(blocks, keep):
+    arr = (vp * max(len(blocks), 1))()
+    for i, b in enumerate(blocks):
+        if b is None:
+            arr[i] = None
+            continue
+        a = np.asfortranarray(np.asarray(b, dtype=np.float64))
+        keep.append(a)
+        arr[i] = a.ctypes.data if a.size else None
+    keep.append(arr)
+    return C.cast(arr, C.POINTER(vp))
+
+
+def _ints(vals, keep):
+    arr = (C.c_int32 * max(len(vals), 1))(*[int(v) for v in vals])
+    keep.append(arr)
+    return C.cast(arr, C.POINTER(C.c_int32))
+
+
+def _cols(b):
+    return 0 if b is None else int(np.asarray(b).shape[1])
+
+
+class Matrix:
+    """A HODLR or HSS matrix resident on the current CUDA device."""
+
+    def __init__(self, handle, kind, tree):
+        self._h = handle
+        self.kind = kind
+        self.tree = tree
+
+    @classmethod
+    def hodlr(cls, tree, g, storage="f64"):
+        keep = []
+        gens = L.hm_hodlr_gens(
+            D=_ptrs(g["D"], keep), U12=_ptrs(g["U12"], keep), V12=_ptrs(g["V12"], keep),
+            U21=_ptrs(g["U21"], keep), V21=_ptrs(g["V21"], keep),
+            k12=_ints([_cols(b) for b in g["U12"]], keep), k21=_ints([_cols(b) for b in g["U21"]], keep))
+        h = vp()
+        check(lib.hm_hodlr_create(tree._h, C.byref(gens), _dtype_code(storage), C.byref(h)), "hm_hodlr_create")
+        return cls(h, "hodlr", tree)
+
+    @classmethod
+    def hss(cls, tree, g, storage="f64"):
+        keep = []
+        Lv = len(g["D"])
+        N = 2 * Lv - 1
+        ku = [0] * N
+        kv = [0] * N
+        for i in range(Lv):
+            ku[Lv - 1 + i] = _cols(g["U"][i])
+            kv[Lv - 1 + i] = _cols(g["V"][i])
+        for q in range(1, Lv - 1):
+            ku[q] = _cols(g["RU"][q])
+            kv[q] = _cols(g["RV"][q])
+        gens = L.hm_hss_gens(
+            D=_ptrs(g["D"], keep), U=_ptrs(g["U"], keep), V=_ptrs(g["V"], keep),
+            RU=_ptrs(g["RU"], keep), RV=_ptrs(g["RV"], keep),
+            B12=_ptrs(g["B12"], keep), B21=_ptrs(g["B21"], keep),
+            ku=_ints(ku, keep), kv=_ints(kv, keep))
+        h = vp()
+        check(lib.hm_hss_create(tree._h, C.byref(gens), _dtype_code(storage), C.byref(h)), "hm_hss_create")
+        return cls(h, "hss", tree)
+
+    @classmethod
+    def create(cls, tree, g, storage="f64"):
+        return cls.hodlr(tree, g, storage) if g["kind"] == "hodlr" else cls.hss(tree, g, storage)
+
+    def info(self):
+        inf = L.hm_matrix_info_t()
+        check(lib.hm_matrix_info(self._h, C.byref(inf)), "hm_matrix_info")
+        return {f: getattr(inf, f) for f, _ in L.hm_matrix_info_t._fields_}
+
+    def generator_bytes(self):
+        b = C.c_size_t()
+        check(lib.hm_matrix_bytes(self._h, C.byref(b)), "hm_matrix_bytes")
+        return b.value
+
+    def reserve(self, r_max):
+        check(lib.hm_matrix_reserve(self._h, int(r_max)), "hm_matrix_reserve")
+
+    def set_path(self, path):
+        check(lib.hm_matrix_set_path(self._h, int(path)), "hm_matrix_set_path")
+
+    def matmat_raw(self, r, X, ldx, xt, Y, ldy, yt, stream=None):
+        """Direct C call with raw pointers (ints) and dtype codes."""
+        f = lib.hm_hodlr_matmat if self.kind == "hodlr" else lib.hm_hss_matmat
+        return check(f(self._h, int(r), vp(X), int(ldx), int(xt), vp(Y), int(ldy), int(yt),
+                       vp(stream) if stream else None), "hm_%s_matmat" % self.kind)
+
+    def matmat(self, X, Y=None, out_dtype=None, stream=None):
+        """Y = A X for an (n, r) column-major tensor/array X; returns Y."""
+        n = self.tree.shape()[0]
+        if torch is not None and isinstance(X, torch.Tensor):
+            X2 = X if X.dim() == 2 else X.reshape(-1, 1)
+            if X2.shape[0] != n:
+                raise ValueError("X must have n rows")
+            r = X2.shape[1]
+            if r > 1 and X2.stride(0) != 1:
+                raise ValueError("X must be column-major (stride(0) == 1); use colmajor()")
+            ldx = X2.stride(1) if r > 1 else max(n, 1)
+            if Y is None:
+                od = out_dtype or (torch.float64 if X2.dtype == torch.float64 else torch.float32)
+                Y = torch.empty((r, n), dtype=od, device=X2.device).t()
+            Y2 = Y if Y.dim() == 2 else Y.reshape(-1, 1)
+            if r > 1 and Y2.stride(0) != 1:
+                raise ValueError("Y must be column-major")
+            ldy = Y2.stride(1) if r > 1 else max(n, 1)
+            if stream is None and X2.is_cuda:
+                stream = torch.cuda.current_stream(X2.device).cuda_stream
+            self.matmat_raw(r, X2.data_ptr(), ldx, _dtype_code(X2.dtype), Y2.data_ptr(), ldy,
+                            _dtype_code(Y2.dtype), stream)
+            return Y
+        Xn = np.asarray(X)
+        if Xn.ndim == 1:
+            Xn = Xn[:, None]
+        Xn = np.asfortranarray(Xn)
+        r = Xn.shape[1]
+        if Y is None:
+            od = out_dtype or (np.float64 if Xn.dtype == np.float64 else np.float32)
+            Y = np.zeros((n, r), dtype=od, order="F")
+        self.matmat_raw(r, Xn.ctypes.data, max(n, 1), _dtype_code(Xn.dtype.type), Y.ctypes.data, max(n, 1),
+                        _dtype_code(Y.dtype.type), stream)
+        return Y
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.hm_destroy(h)
+            self._h = None
+
+
+def colmajor(t):
+    """Column-major copy of a 2-D torch tensor (layout helper for callers)."""
+    return t.t().contiguous().t()
+
+
+def device_status(stream=None):
+    check(lib.hm_device_status(vp(stream) if stream else None), "hm_device_status")

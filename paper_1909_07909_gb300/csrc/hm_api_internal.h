@@ -1,0 +1,88 @@
+// Host-side objects of libhm (trees, matrices) and helpers shared by the
+// runtime translation units (products, batching, serving).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "hm_internal.h"
+
+namespace hmi {
+
+constexpr uint32_t kMagicTree = 0x31545248u;     // "HRT1"
+constexpr uint32_t kMagicMatrix = 0x314d5248u;   // "HRM1"
+constexpr uint32_t kMagicBatch = 0x31425248u;    // "HRB1"
+constexpr uint32_t kMagicServer = 0x31535248u;   // "HRS1"
+
+// A typed generator plane being packed on the host (hi and, for BF16X2, lo).
+struct Plane {
+  int storage = HM_F64;
+  size_t count = 0;
+  std::vector<uint8_t> hi, lo;
+  void init(int st, size_t cnt);
+  void set(size_t i, double v);
+};
+
+uint16_t f64_to_bf16(double a);
+double bf16_to_f64(uint16_t h);
+size_t storage_bytes(int st);
+int* device_error_word(int dev);
+const double* host_block(const double* p, size_t count, std::vector<double>& tmp);
+
+}  // namespace hmi
+
+struct hm_tree {
+  uint32_t magic;
+  int64_t n;
+  int p;
+  int L;
+  std::vector<int64_t> ends;
+};
+
+struct hm_matrix {
+  uint32_t magic = 0;
+  int kind = 0;
+  int storage = 0;
+  int device = 0;
+  int64_t n = 0;
+  int p = 0, L = 1;
+  std::vector<int64_t> ends;
+  int m_max = 0, m_pad = 16, Ke = 0, Kp = 0, We = 16;
+  int kk[hmi::kMaxDepth + 2] = {0};
+  int koff[hmi::kMaxDepth + 2] = {0};
+  int64_t gen_elems = 0;
+  size_t gen_bytes = 0;
+  size_t dev_bytes = 0;
+  int64_t* d_off = nullptr;
+  void* d_A = nullptr;
+  void* d_A_lo = nullptr;
+  void* d_W = nullptr;
+  void* d_W_lo = nullptr;
+  void* d_RU = nullptr;
+  void* d_RVt = nullptr;
+  void* d_B12 = nullptr;
+  void* d_B21 = nullptr;
+  int64_t r_cap = 0;
+  void* d_ws = nullptr;
+  int* d_cnt = nullptr;
+  void* d_io = nullptr;
+  size_t io_cap = 0;
+  int* err = nullptr;
+  int path = 0;
+  hmi::MatView view() const;
+};
+
+namespace hmi {
+
+int64_t node_start(const hm_tree* t, int q);
+int64_t node_end(const hm_tree* t, int q);
+hm_status ensure_scratch(hm_matrix* A, int64_t r);
+Scratch scratch_of(const hm_matrix* A, int64_t r);
+hm_status run_product(const hm_matrix* A, int want_kind, int64_t r, const void* X, int64_t ldx, int xt,
+                      void* Y, int64_t ldy, int yt, void* stream);
+hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                         int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t s);
+// Releases batch and server objects (defined with them).
+void destroy_other(void* any, uint32_t magic);
+
+}  // namespace hmi

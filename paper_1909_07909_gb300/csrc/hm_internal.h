@@ -1,0 +1,94 @@
+// Internal structures of libhm shared by the host runtime and the kernels.
+//
+// Device layout of one matrix (all generator planes row-major, storage type S):
+//
+//  * Expansion operand  Aexp: n rows x We columns, We = m_pad + Ke.  Row g of
+//    leaf i holds [ D_i(g,:) | 0 ... | E_i(g,:) ] where the D part occupies
+//    columns [0, m_i), zeros fill [m_i, m_pad) and E_i starts at column m_pad:
+//      HODLR: E_i = [U^(1)(g,:) | ... | U^(p)(g,:)], the row factors of the
+//             leaf's ancestors at levels 1..p (level l block at koff[l], width kk[l]);
+//      HSS:   E_i = U_i(g,:), the leaf row basis.
+//    One leaf's output block is then a single product
+//      Y(I_i, :) = [D_i | E_i] [X(I_i, :); Z_i]
+//    with Z_i the per-level T's (HODLR) or the leaf y-hat (HSS).
+//  * Projection operand Wprj: L*Kp rows x m_pad columns; rows i*Kp .. i*Kp+Kp-1
+//    hold the transposed column factors of leaf i's rows (HODLR: the V of each
+//    level, at the same offsets koff[l]; HSS: V_i^T), zero-padded to m_pad.
+//  * HSS tree operators in the compute type C (double for F64 storage, float
+//    otherwise), one block per internal node q (0..L-2):
+//      RU  : 2Ke x Ke  rows [0,Ke) = Rl (left child), [Ke,2Ke) = Rr
+//      RVt : Kp x 2Kp  = R_V^T, columns [0,Kp) act on the left child
+//      B12 : Ke x Kp,  B21 : Ke x Kp
+//    (root entries of RU/RVt are unused).
+//
+// Scratch of one product with r columns (compute type C), node-major:
+//  HODLR  PS[node][col][e], e < Ke: a leaf holds V^T X of its rows for every
+//         level; an internal node at level l holds, in rows of levels 1..l, the
+//         sums over its leaves, so PS[node][.][koff[l]..] is T_node^(l).
+//  HSS    xh[node][col][e] (e < Kp), yc / yf [node][col][e] (e < Ke).
+//  cnt    (L-1) x nchunks arrival counters, zero before and after every call.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "hm.h"
+
+namespace hmi {
+
+constexpr int kMaxDepth = 30;
+
+struct MatView {
+  int kind;      // hm_kind
+  int storage;   // hm_dtype
+  int p, L;
+  int m_pad;     // padded leaf width (multiple of 16)
+  int Ke;        // width of the expansion factor part (multiple of 8)
+  int Kp;        // projection rows per leaf (multiple of 8)
+  int We;        // m_pad + Ke
+  int64_t n;
+  const int64_t* off;   // device, L+1 leaf offsets
+  const void* A;        // expansion operand (hi plane for BF16X2)
+  const void* A_lo;     // lo plane (BF16X2) or nullptr
+  const void* W;        // projection operand
+  const void* W_lo;
+  const void* RU;       // HSS tree operators (compute type)
+  const void* RVt;
+  const void* B12;
+  const void* B21;
+  int kk[kMaxDepth + 2];    // HODLR padded rank of level l (index 1..p)
+  int koff[kMaxDepth + 2];  // HODLR offset of level l inside the Ke block
+};
+
+struct Scratch {
+  void* PS;   // HODLR partial sums
+  void* xh;   // HSS
+  void* yc;
+  void* yf;
+  int* cnt;
+  int* err;   // device error word (bounded waits)
+};
+
+// Launches the SIMT path (all storage types, any r).  Defined in k_simt_*.cu.
+hm_status launch_simt(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx,
+                      int xt, void* Y, int64_t ldy, int yt, cudaStream_t s);
+
+// Per-storage-type entry points of the SIMT path.
+hm_status launch_simt_f64(const MatView&, const Scratch&, int64_t, const void*, int64_t, int, void*,
+                          int64_t, int, cudaStream_t);
+hm_status launch_simt_f32(const MatView&, const Scratch&, int64_t, const void*, int64_t, int, void*,
+                          int64_t, int, cudaStream_t);
+hm_status launch_simt_bf16(const MatView&, const Scratch&, int64_t, const void*, int64_t, int, void*,
+                           int64_t, int, cudaStream_t);
+hm_status launch_simt_bf16x2(const MatView&, const Scratch&, int64_t, const void*, int64_t, int,
+                             void*, int64_t, int, cudaStream_t);
+
+// Scratch element counts for r columns (in compute-type elements) and counter count.
+size_t scratch_elems(const MatView& mv, int64_t r);
+size_t counter_count(const MatView& mv, int64_t r);
+
+void set_error(const char* fmt, ...);
+
+}  // namespace hmi

@@ -1,0 +1,11 @@
+// SIMT kernels instantiated for HM_BF16 storage (see k_simt.cuh).
+#include "k_simt.cuh"
+
+namespace hmi {
+
+hm_status launch_simt_bf16(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx,
+                        int xt, void* Y, int64_t ldy, int yt, cudaStream_t s) {
+  return launch_simt_t<HM_BF16>(mv, ws, r, X, ldx, xt, Y, ldy, yt, s);
+}
+
+}  // namespace hmi
