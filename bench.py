@@ -1,0 +1,459 @@
+#!/usr/bin/env python3
+"""Throughput of the HSS matrix-times-block product on GB300.
+
+Workload (one "step" = one product Y = A X through the C ABI):
+  HSS, n = 65536, leaf 256 (p = 8), nested rank 32, 64 right-hand sides;
+  leaf U, V orthonormal (Q of a Gaussian QR), translations R and couplings B
+  iid N(0, 1/32) (variance), D ~ N(0,1) + 8 I, X ~ N(0,1); seeded.
+  Headline storage: --precision (default bf16) with float32 X and Y; the
+  other storages (f64, f32, bf16x2) are timed as variants in the same run.
+
+Timing: W untimed steps, then exactly K steps bracketed by a barrier and
+torch.cuda.synchronize() on both sides, CUDA events on the launching stream,
+max over ranks.  The inputs rotate over several resident copies whose total
+exceeds the 135 MB L2, so every step streams its generators from HBM.
+
+--impl reference times the CPU oracle (the FP64 dense-definition product)
+on a bounded sample of the same workload.  N > 1 (torchrun): each rank runs
+its own replica (weak scaling, no collective on the data path).
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HSS/HODLR matvec GB/s, % of roofline, mixed vs FP64 at stated err; p99 ms"
+N_, LEAF, RANK, RHS = 65536, 256, 32, 64
+WORKLOAD = "hss_matmat n=65536 leaf=256 rank=32 rhs=64"
+ESZ = {"f64": 8, "f32": 4, "bf16": 2, "bf16x2": 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="hm", choices=["hm", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "f32", "f64", "bf16x2"])
+    ap.add_argument("--copies", type=int, default=0, help="resident copies (0 = enough to exceed L2)")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-leaves", type=int, default=6, help="leaf row blocks in the CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), \
+        int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 / FP32 FMA peaks of this GPU model (FMA-throughput probe, profiles/fma_peaks_probe.txt).
+FP64_TFLOPS = 1.199
+FP32_TFLOPS = 74.9
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        loaded = [v for v in sm if v > 0.5 * (mx or max(sm))] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs():
+    import workloads as W
+    rng = W.rng_for(2)
+    import paper_1909_07909_gb300 as hm
+    tree = hm.Tree.default(N_, LEAF)
+    c = tree.leaf_ends
+    g = W.random_hss(rng, c, RANK)
+    X = rng.standard_normal((N_, RHS))
+    return tree, c, g, X
+
+
+def step_bytes(A, storage, xs=4, ys=4):
+    return A.generator_bytes() + N_ * RHS * (xs + ys)
+
+
+PHASES = ["project", "tree_up", "tree_down", "expand"]
+
+
+def phase_bytes(storage, c, xs=None):
+    """Algorithmic bytes per launch: the expansion reads D and U, X and writes
+    Y; the projection reads V and X; the tree kernels move only k x r blocks
+    (per-level intermediates are excluded, as for the whole step)."""
+    s = ESZ[storage]
+    xs = xs or (8 if storage == "f64" else 4)
+    sizes = [c[0]] + [c[i] - c[i - 1] for i in range(1, len(c))]
+    d_elems = sum(m * m for m in sizes)
+    expand = (d_elems + N_ * RANK) * s + N_ * RHS * (xs + xs)
+    project = N_ * RANK * s + N_ * RHS * xs
+    return {"project": project, "tree_up": 0, "tree_down": 0, "expand": expand}
+
+
+def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases, clock_index=None,
+                 prof_steps=None):
+    """Device throughput of one storage type (timed region without profiling
+    events, so consecutive kernels overlap), then a profiled pass that brackets
+    every kernel with CUDA events for per-kernel durations."""
+    td = torch.float64 if storage == "f64" else torch.float32
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mats = [hm.Matrix.create(tree, g, storage) for _ in range(copies)]
+    Xh = torch.from_numpy(g["_X"].T.copy())
+    Xs = [Xh.to(dev).to(td).t() for _ in range(copies)]
+    Ys = [torch.empty((RHS, N_), dtype=td, device=dev).t() for _ in range(copies)]
+    for A in mats:
+        A.reserve(RHS)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    code = hm.HM_F64 if storage == "f64" else hm.HM_F32
+
+    def run(i):
+        j = i % copies
+        mats[j].matmat_raw(RHS, Xs[j].data_ptr(), N_, code, Ys[j].data_ptr(), N_, code, sptr)
+
+    for i in range(warmup):
+        run(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(clock_index) if clock_index is not None else None
+    if sampler:
+        sampler.__enter__()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        run(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__()
+    ms_total = e0.elapsed_time(e1)
+    phases = None
+    if want_phases:
+        ps = prof_steps or steps
+        for A in mats:
+            A.profile(True)
+            A.phase_times()
+        for i in range(ps):
+            run(i)
+        torch.cuda.synchronize()
+        acc_ms = [0.0] * 4
+        acc_n = [0] * 4
+        for A in mats:
+            ms, n = A.phase_times()
+            A.profile(False)
+            for k in range(4):
+                acc_ms[k] += ms[k]
+                acc_n[k] += n[k]
+        phases = {"ms": acc_ms, "launches": acc_n, "steps": ps}
+    es = 8 if storage == "f64" else 4
+    res = {"ms_total": ms_total, "ms_per_step": ms_total / steps,
+           "bytes_per_step": step_bytes(mats[0], storage, es, es),
+           "phases": phases, "clocks": sampler.summary() if sampler else None,
+           "generator_bytes": mats[0].generator_bytes()}
+    res["gbs"] = res["bytes_per_step"] / (res["ms_per_step"] * 1e-3) / 1e9
+    Y0 = Ys[0].to(torch.float64).cpu().numpy()
+    del mats
+    return res, Y0
+
+
+def e2e_host(hm, torch, tree, g, storage, steps):
+    """Same product through the C ABI with pinned host buffers (copies inside)."""
+    import numpy as np
+    A = hm.Matrix.create(tree, g, storage)
+    A.reserve(RHS)
+    f64 = storage == "f64"
+    td = torch.float64 if f64 else torch.float32
+    Xp = torch.from_numpy(g["_X"].T.copy()).to(td).pin_memory()
+    Yp = torch.empty((RHS, N_), dtype=td).pin_memory()
+    code = hm.HM_F64 if f64 else hm.HM_F32
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        A.matmat_raw(RHS, Xp.data_ptr(), N_, code, Yp.data_ptr(), N_, code, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        A.matmat_raw(RHS, Xp.data_ptr(), N_, code, Yp.data_ptr(), N_, code, stream)
+    dt = (time.perf_counter() - t0) / steps
+    es = 8 if f64 else 4
+    b = A.generator_bytes() + N_ * RHS * 2 * es
+    del np
+    return {"value": b / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": N_ * RHS * es,
+            "d2h_bytes_per_step": N_ * RHS * es, "ms_per_step": dt * 1e3}
+
+
+def fp64_step_bytes(c):
+    """Algorithmic bytes of one FP64 product: all generators read once, X read, Y written."""
+    L = len(c)
+    sizes = [c[0]] + [c[i] - c[i - 1] for i in range(1, L)]
+    elems = sum(m * m for m in sizes) + 2 * N_ * RANK + max(L - 2, 0) * 4 * RANK * RANK + \
+        max(2 * L - 2, 0) * RANK * RANK
+    return 8 * elems + N_ * RHS * 16
+
+
+def cpu_oracle_sample(c, g, X, leaves):
+    """Oracle (dense-definition product) on `leaves` leaf row blocks; returns
+    (seconds, rows, Yrows, cores)."""
+    import numpy as np
+    from oracle import matmat as OM
+    from oracle import tree as OT
+    t0 = time.perf_counter()
+    blocks = OM.matmat_leaves(c, g, X, leaves)
+    dt = time.perf_counter() - t0
+    rows = []
+    for i in leaves:
+        a, b = OT.leaf_range(c, i)
+        rows.extend(range(a, b))
+    return dt, rows, np.vstack(blocks)
+
+
+def traffic_for(kernel_key):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json, if the kernel
+    source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    ent = rec.get(kernel_key)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for f in ent.get("sources", []):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != ent.get("sha256"):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import workloads as W
+    from oracle import tree as OT
+    rng = W.rng_for(2)
+    c = OT.default_leaf_ends(N_, LEAF)
+    g = W.random_hss(rng, c, RANK)
+    X = rng.standard_normal((N_, RHS))
+    L = len(c)
+    per = max(1, args.cpu_leaves)
+    for i in range(args.warmup):
+        cpu_oracle_sample(c, g, X, [(i * per + j) % L for j in range(per)])
+    t = 0.0
+    for i in range(args.steps):
+        dt, _, _ = cpu_oracle_sample(c, g, X, [((i + args.warmup) * per + j) % L for j in range(per)])
+        t += dt
+    frac = per / L
+    nbytes = fp64_step_bytes(c)
+    step_s = t / args.steps / frac
+    val = nbytes / step_s / 1e9
+    cores = os.cpu_count()
+    sample = "%d of %d leaf row blocks per step (scaled by %d)" % (per, L, L // per)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "storage": "f64", "oracle": "dense definition, FP64 numpy/BLAS"},
+           "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    del np
+    return 0
+
+
+def main():
+    args = parse()
+    rank, local, world = dist_env()
+    if args.impl == "reference":
+        return run_reference(args)
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", str(os.cpu_count()))
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    import paper_1909_07909_gb300 as hm
+
+    peaks, peak_src = measured_peaks()
+    tree, c, g, X = make_inputs()
+    g["_X"] = X
+    prec = args.precision
+    gen_bytes_est = {"bf16": 45e6, "f32": 90e6, "bf16x2": 90e6, "f64": 180e6}[prec]
+    io = N_ * RHS * (16 if prec == "f64" else 8)
+    copies = args.copies or max(2, math.ceil(2.2 * 135.5e6 / (gen_bytes_est + io)))
+
+    if world > 1:
+        torch.distributed.barrier()
+    head, Yh = time_variant(hm, torch, tree, g, prec, args.steps, args.warmup, copies, True,
+                            clock_index=local, prof_steps=min(args.steps, 200))
+    # whole-job time: max over ranks of this rank's timed region
+    t_local = torch.tensor([head["ms_total"]], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    ms_max = float(t_local.item())
+    value = world * head["bytes_per_step"] * args.steps / (ms_max * 1e-3) / 1e9
+
+    # dominant kernel roofline (per-kernel durations from the profiled pass)
+    pb = phase_bytes(prec, c)
+    ph = head["phases"]
+    dom = max(range(4), key=lambda k: ph["ms"][k])
+    avg_ms = ph["ms"][dom] / max(ph["launches"][dom], 1)
+    achieved = pb[PHASES[dom]] / (avg_ms * 1e-3) / 1e9
+    kernel_key = "%s_%s" % (PHASES[dom], prec)
+    if prec == "f64":
+        flops = {"project": 2 * N_ * RANK * RHS, "tree_up": 0, "tree_down": 0,
+                 "expand": 2 * (N_ * LEAF + N_ * RANK) * RHS}[PHASES[dom]]
+        roof = {"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": FP64_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "FP64 FMA probe (profiles/fma_peaks_probe.txt)"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": peak_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(kernel_key)
+    roof["kernel"] = kernel_key
+    roof["ms_per_launch"] = avg_ms
+    roof["phase_ms_per_step"] = {PHASES[k]: ph["ms"][k] / ph["steps"] for k in range(4)}
+    roof["expand_frac_of_hbm"] = (pb["expand"] / (ph["ms"][3] / max(ph["launches"][3], 1) * 1e-3) / 1e9
+                                  / peaks["hbm_gbs"]) if ph["launches"][3] else None
+
+    out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16",
+                                                              "bf16x2": "bf16x2"}[prec],
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": N_, "leaf": LEAF, "rank": RANK, "rhs": RHS, "storage": prec,
+                      "x_dtype": "f64" if prec == "f64" else "f32", "y_dtype": "f64" if prec == "f64" else "f32",
+                      "l2": "inputs larger than L2: %d rotating resident copies of %.1f MB" %
+                            (copies, head["bytes_per_step"] / 1e6),
+                      "generators": "leaf U,V orthonormal; R,B iid N(0,1/32) (variance); D=N(0,1)+8I; X=N(0,1)",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "roofline": roof,
+           "gpu_launches": int(sum(ph["launches"]) * args.steps / ph["steps"]),
+           "clocks": head["clocks"]}
+
+    if rank == 0:
+        out["e2e"] = e2e_host(hm, torch, tree, g, prec, max(5, min(50, args.steps // 4)))
+        variants = {}
+        ys = {prec: Yh}
+        if not args.no_variants:
+            for v in ["f64", "f32", "bf16", "bf16x2"]:
+                if v == prec:
+                    continue
+                eb = {"bf16": 45e6, "f32": 90e6, "bf16x2": 90e6, "f64": 180e6}[v] + N_ * RHS * (16 if v == "f64" else 8)
+                cps = max(2, math.ceil(2.2 * 135.5e6 / eb))
+                st = 20 if v == "f64" else max(20, args.steps // 4)
+                r_, yv = time_variant(hm, torch, tree, g, v, st, 3, cps, True, prof_steps=min(st, 20))
+                ys[v] = yv
+                pbv = phase_bytes(v, c)
+                d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
+                am = r_["phases"]["ms"][d] / max(r_["phases"]["launches"][d], 1)
+                variants[v] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
+                               "dominant_kernel": PHASES[d],
+                               "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
+                                                     for k in range(4)}}
+                if pbv[PHASES[d]]:
+                    variants[v]["dominant_gbs"] = pbv[PHASES[d]] / (am * 1e-3) / 1e9
+        if not args.no_cpu and world == 1:
+            leaves = [0, 1, 127, 128, 200, 255][: max(1, args.cpu_leaves)]
+            dt, rows, Yo = cpu_oracle_sample(c, g, X, leaves)
+            frac = len(leaves) / len(c)
+            bytes64 = fp64_step_bytes(c)
+            est = dt / frac
+            out["cpu_baseline"] = {"value": bytes64 / est / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
+                                   "kind": "oracle",
+                                   "sample": "%d of %d leaf row blocks of one product, %.2f s, scaled by %.1f"
+                                             % (len(leaves), len(c), dt, 1 / frac)}
+            errs = {}
+            for v, Yv in ys.items():
+                num = np.linalg.norm(Yv[rows] - Yo, axis=0)
+                den = np.linalg.norm(Yo, axis=0)
+                errs[v] = float(np.max(num / den))
+            out["err_vs_oracle"] = {"metric": "max over columns of ||y - y_oracle||_2/||y_oracle||_2 on %d sampled rows"
+                                              % len(rows), **errs}
+            for v in variants:
+                variants[v]["err_vs_oracle"] = errs.get(v)
+        if variants:
+            out["variants"] = variants
+            if "f64" in variants and prec != "f64":
+                out["mixed_vs_fp64_speedup"] = value / world / variants["f64"]["value"]
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

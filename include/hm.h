@@ -199,6 +199,19 @@ hm_status hm_device_status(void* stream);
  * BF16X2), 1 = SIMT only, 2 = tensor cores whenever supported. */
 hm_status hm_matrix_set_path(hm_matrix* A, int32_t path);
 
+/* Per-kernel timing of later products on this matrix: with enable = 1 every
+ * kernel launch of a product is bracketed by CUDA events recorded on the
+ * product's stream; enable = 0 stops recording.  Not for use under CUDA-graph
+ * capture. */
+hm_status hm_matrix_profile(hm_matrix* A, int32_t enable);
+
+/* Device time accumulated per phase since the last read, in milliseconds,
+ * and the number of launches: phase 0 = leaf projection (V^T X), 1 = tree
+ * upsweep (HSS: translations R_V and couplings; HODLR: per-level sums),
+ * 2 = HSS downsweep, 3 = leaf expansion.  Waits for the recorded events, then
+ * resets the accumulators. */
+hm_status hm_matrix_phase_times(hm_matrix* A, double ms[4], int64_t launches[4]);
+
 /* Releases any object created by this library (tree, matrix, batch, server).
  * NULL-safe.  A matrix registered with a server must be released after the
  * server. */

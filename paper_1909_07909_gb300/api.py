@@ -163,6 +163,17 @@ class Matrix:
     def set_path(self, path):
         check(lib.hm_matrix_set_path(self._h, int(path)), "hm_matrix_set_path")
 
+    def profile(self, enable=True):
+        """Bracket every kernel launch of later products with CUDA events."""
+        check(lib.hm_matrix_profile(self._h, 1 if enable else 0), "hm_matrix_profile")
+
+    def phase_times(self):
+        """(ms[4], launches[4]) per phase (projection, tree up, HSS down, expansion) since the last read."""
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        check(lib.hm_matrix_phase_times(self._h, ms, n), "hm_matrix_phase_times")
+        return list(ms), list(n)
+
     def matmat_raw(self, r, X, ldx, xt, Y, ldy, yt, stream=None):
         """Direct C call with raw pointers (ints) and dtype codes."""
         f = lib.hm_hodlr_matmat if self.kind == "hodlr" else lib.hm_hss_matmat

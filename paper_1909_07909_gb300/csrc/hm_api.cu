@@ -293,7 +293,7 @@ hmi::MatView hm_matrix::view() const {
   v.W = d_W;
   v.W_lo = d_W_lo;
   v.RU = d_RU;
-  v.RVt = d_RVt;
+  v.RV = d_RVt;
   v.B12 = d_B12;
   v.B21 = d_B21;
   for (int l = 0; l <= kMaxDepth + 1; ++l) {
@@ -328,6 +328,7 @@ static hm_status finish_create(hm_matrix* A, const hm_tree* t, Plane& Ap, Plane&
     return s;
   }
   A->dev_bytes = dev;
+  make_tensor_maps(A);
   A->err = device_error_word(A->device);
   if (!A->err) {
     free_matrix_device(A);
@@ -504,12 +505,16 @@ extern "C" hm_status hm_hss_create(const hm_tree* t, const hm_hss_gens* g, hm_dt
     if (dbl) reinterpret_cast<double*>(buf.data())[idx] = v;
     else reinterpret_cast<float*>(buf.data())[idx] = static_cast<float>(v);
   };
+  // Device layouts (compute type), one block per internal node q:
+  //   RUt[q][h][j][i] = R_U(h*Ke + i, j)  -- the child half h of R_U, transposed
+  //   RV [q][j][i]    = R_V(j, i)         -- rows of the stacked children, row-major
+  //   B12t[q][j][i]   = B12(i, j), B21t[q][j][i] = B21(i, j)
   std::vector<uint8_t> RU, RVt, B12, B21;
   const size_t nI = static_cast<size_t>(std::max(L - 1, 0));
   RU.assign(nI * 2 * Ke * Ke * cs, 0);
-  RVt.assign(nI * Kp * 2 * Kp * cs, 0);
-  B12.assign(nI * Ke * Kp * cs, 0);
-  B21.assign(nI * Ke * Kp * cs, 0);
+  RVt.assign(nI * 2 * Kp * Kp * cs, 0);
+  B12.assign(nI * Kp * Ke * cs, 0);
+  B21.assign(nI * Kp * Ke * cs, 0);
   int64_t telems = 0;
   for (int q = 0; q < L - 1; ++q) {
     const int a = 2 * q + 1, b = 2 * q + 2;
@@ -519,27 +524,28 @@ extern "C" hm_status hm_hss_create(const hm_tree* t, const hm_hss_gens* g, hm_dt
       const double* R = host_block(g->RU[q], static_cast<size_t>((kua + kub) * kuq), tmp);
       if ((kua + kub) * kuq > 0 && !R) { delete A; return fail(HM_EINVAL, "RU[%d] missing", q); }
       for (int rr = 0; rr < kua + kub; ++rr) {
-        const int prow = rr < kua ? rr : Ke + (rr - kua);
-        for (int cc = 0; cc < kuq; ++cc)
-          put(RU, (static_cast<size_t>(q) * 2 * Ke + prow) * Ke + cc, R[rr + cc * (kua + kub)]);
+        const int h = rr < kua ? 0 : 1;
+        const int i = rr < kua ? rr : rr - kua;
+        for (int j = 0; j < kuq; ++j)
+          put(RU, ((static_cast<size_t>(q) * 2 + h) * Ke + j) * Ke + i, R[rr + j * (kua + kub)]);
       }
       const double* W = host_block(g->RV[q], static_cast<size_t>((kva + kvb) * kvq), tmp);
       if ((kva + kvb) * kvq > 0 && !W) { delete A; return fail(HM_EINVAL, "RV[%d] missing", q); }
       for (int rr = 0; rr < kva + kvb; ++rr) {
         const int prow = rr < kva ? rr : Kp + (rr - kva);
         for (int cc = 0; cc < kvq; ++cc)
-          put(RVt, (static_cast<size_t>(q) * Kp + cc) * 2 * Kp + prow, W[rr + cc * (kva + kvb)]);
+          put(RVt, (static_cast<size_t>(q) * 2 * Kp + prow) * Kp + cc, W[rr + cc * (kva + kvb)]);
       }
       telems += static_cast<int64_t>(kua + kub) * kuq + static_cast<int64_t>(kva + kvb) * kvq;
     }
     const double* S12 = host_block(g->B12[q], static_cast<size_t>(kua * kvb), tmp);
     if (kua * kvb > 0 && !S12) { delete A; return fail(HM_EINVAL, "B12[%d] missing", q); }
     for (int i = 0; i < kua; ++i)
-      for (int j = 0; j < kvb; ++j) put(B12, (static_cast<size_t>(q) * Ke + i) * Kp + j, S12[i + j * kua]);
+      for (int j = 0; j < kvb; ++j) put(B12, (static_cast<size_t>(q) * Kp + j) * Ke + i, S12[i + j * kua]);
     const double* S21 = host_block(g->B21[q], static_cast<size_t>(kub * kva), tmp);
     if (kub * kva > 0 && !S21) { delete A; return fail(HM_EINVAL, "B21[%d] missing", q); }
     for (int i = 0; i < kub; ++i)
-      for (int j = 0; j < kva; ++j) put(B21, (static_cast<size_t>(q) * Ke + i) * Kp + j, S21[i + j * kub]);
+      for (int j = 0; j < kva; ++j) put(B21, (static_cast<size_t>(q) * Kp + j) * Ke + i, S21[i + j * kub]);
     telems += static_cast<int64_t>(kua) * kvb + static_cast<int64_t>(kub) * kva;
   }
   A->gen_elems = elems + telems;
@@ -696,7 +702,8 @@ hm_status run_product(const hm_matrix* Ac, int want_kind, int64_t r, const void*
     }
   }
   const MatView mv = A->view();
-  const Scratch ws = scratch_of(A, r);
+  Scratch ws = scratch_of(A, r);
+  ws.prof = A->prof;
   st = launch_product(A, mv, ws, r, Xd, ldxd, xt, Yd, ldyd, yt, s);
   if (st != HM_OK) return st;
   if (!ydev) {
@@ -708,16 +715,102 @@ hm_status run_product(const hm_matrix* Ac, int want_kind, int64_t r, const void*
 
 hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                          int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t s) {
-  (void)A;
-  switch (mv.storage) {
-    case HM_F64: return launch_simt_f64(mv, ws, r, X, ldx, xt, Y, ldy, yt, s);
-    case HM_F32: return launch_simt_f32(mv, ws, r, X, ldx, xt, Y, ldy, yt, s);
-    case HM_BF16: return launch_simt_bf16(mv, ws, r, X, ldx, xt, Y, ldy, yt, s);
-    default: return launch_simt_bf16x2(mv, ws, r, X, ldx, xt, Y, ldy, yt, s);
+  auto phase = [&](int ph, bool pdl) -> hm_status {
+    switch (mv.storage) {
+      case HM_F64: return simt_phase_f64(ph, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
+      case HM_F32: return simt_phase_f32(ph, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
+      case HM_BF16: return simt_phase_bf16(ph, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
+      default: return simt_phase_bf16x2(ph, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
+    }
+  };
+  hm_status st = phase(0, false);
+  if (st != HM_OK) return st;
+  st = phase(1, true);
+  if (st != HM_OK) return st;
+  st = phase(2, true);
+  if (st != HM_OK) return st;
+  if (use_tensor_cores(A, r)) {
+    st = launch_expand_tc(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, true);
+    if (st != HM_EUNSUPPORTED) return st;
   }
+  return phase(3, true);
 }
 
 }  // namespace hmi
+
+namespace hmi {
+
+cudaEvent_t EventProf::get() {
+  if (!pool_.empty()) {
+    cudaEvent_t e = pool_.back();
+    pool_.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void EventProf::mark(int phase, bool start, cudaStream_t s) {
+  cudaEvent_t e = get();
+  cudaEventRecord(e, s);
+  if (start) {
+    open_[phase] = e;
+  } else {
+    recs_.push_back({phase, open_[phase], e});
+    open_[phase] = nullptr;
+  }
+}
+
+hm_status EventProf::read(double ms[4], int64_t launches[4]) {
+  for (auto& r : recs_) {
+    HM_CUDA(cudaEventSynchronize(r.b), "event synchronize");
+    float t = 0.f;
+    HM_CUDA(cudaEventElapsedTime(&t, r.a, r.b), "event elapsed");
+    ms_[r.phase] += t;
+    n_[r.phase] += 1;
+    pool_.push_back(r.a);
+    pool_.push_back(r.b);
+  }
+  recs_.clear();
+  for (int i = 0; i < 4; ++i) {
+    ms[i] = ms_[i];
+    launches[i] = n_[i];
+    ms_[i] = 0;
+    n_[i] = 0;
+  }
+  return HM_OK;
+}
+
+EventProf::~EventProf() {
+  for (auto& r : recs_) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : pool_) cudaEventDestroy(e);
+}
+
+}  // namespace hmi
+
+extern "C" hm_status hm_matrix_profile(hm_matrix* A, int32_t enable) {
+  if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
+  if (enable && !A->prof) A->prof = new (std::nothrow) EventProf();
+  if (!enable && A->prof) {
+    delete A->prof;
+    A->prof = nullptr;
+  }
+  return HM_OK;
+}
+
+extern "C" hm_status hm_matrix_phase_times(hm_matrix* A, double ms[4], int64_t launches[4]) {
+  if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
+  if (!ms || !launches) return fail(HM_EINVAL, "output arrays are NULL");
+  if (!A->prof) {
+    for (int i = 0; i < 4; ++i) { ms[i] = 0; launches[i] = 0; }
+    return HM_OK;
+  }
+  return static_cast<EventProf*>(A->prof)->read(ms, launches);
+}
 
 extern "C" hm_status hm_matrix_reserve(hm_matrix* A, int64_t r_max) {
   if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
@@ -768,6 +861,8 @@ extern "C" void hm_destroy(void* any) {
     int dev_prev = -1;
     cudaGetDevice(&dev_prev);
     if (dev_prev != A->device) cudaSetDevice(A->device);
+    delete A->prof;
+    A->prof = nullptr;
     free_matrix_device(A);
     if (dev_prev != A->device) cudaSetDevice(dev_prev);
     delete A;

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda.h>
+
 #include "hm_internal.h"
 
 namespace hmi {
@@ -69,6 +71,10 @@ struct hm_matrix {
   size_t io_cap = 0;
   int* err = nullptr;
   int path = 0;
+  hmi::Prof* prof = nullptr;   // set while profiling is enabled
+  CUtensorMap tmA;              // TMA descriptors of the expansion planes (BF16 / BF16X2)
+  CUtensorMap tmAlo;
+  bool tm_ok = false;
   hmi::MatView view() const;
 };
 
@@ -77,11 +83,34 @@ namespace hmi {
 int64_t node_start(const hm_tree* t, int q);
 int64_t node_end(const hm_tree* t, int q);
 hm_status ensure_scratch(hm_matrix* A, int64_t r);
+
+// CUDA-event timing of the phases of the products of one matrix.
+class EventProf : public Prof {
+ public:
+  void mark(int phase, bool start, cudaStream_t s) override;
+  hm_status read(double ms[4], int64_t launches[4]);
+  ~EventProf() override;
+
+ private:
+  struct Rec { int phase; cudaEvent_t a, b; };
+  std::vector<Rec> recs_;
+  std::vector<cudaEvent_t> pool_;
+  cudaEvent_t open_[4] = {nullptr, nullptr, nullptr, nullptr};
+  double ms_[4] = {0, 0, 0, 0};
+  int64_t n_[4] = {0, 0, 0, 0};
+  cudaEvent_t get();
+};
 Scratch scratch_of(const hm_matrix* A, int64_t r);
 hm_status run_product(const hm_matrix* A, int want_kind, int64_t r, const void* X, int64_t ldx, int xt,
                       void* Y, int64_t ldy, int yt, void* stream);
 hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                          int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t s);
+// Tensor-core expansion (k_tc.cu).
+void make_tensor_maps(hm_matrix* A);
+bool use_tensor_cores(const hm_matrix* A, int64_t r);
+hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                           int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl);
+
 // Releases batch and server objects (defined with them).
 void destroy_other(void* any, uint32_t magic);
 

@@ -15,11 +15,13 @@
 //    hold the transposed column factors of leaf i's rows (HODLR: the V of each
 //    level, at the same offsets koff[l]; HSS: V_i^T), zero-padded to m_pad.
 //  * HSS tree operators in the compute type C (double for F64 storage, float
-//    otherwise), one block per internal node q (0..L-2):
-//      RU  : 2Ke x Ke  rows [0,Ke) = Rl (left child), [Ke,2Ke) = Rr
-//      RVt : Kp x 2Kp  = R_V^T, columns [0,Kp) act on the left child
-//      B12 : Ke x Kp,  B21 : Ke x Kp
-//    (root entries of RU/RVt are unused).
+//    otherwise), one block per internal node q (0..L-2), stored so that every
+//    product reads them as "transposed" matrices Mt[j][i] (inner index i
+//    contiguous, which is conflict-free for consecutive threads):
+//      RU  [q][h][j][i] = R_U(h*Ke + i, j)   (h = 0 left child half, 1 right)
+//      RV  [q][j][i]    = R_V(j, i), j over the stacked children (2Kp rows)
+//      B12 [q][j][i]    = B12(i, j),  B21 [q][j][i] = B21(i, j)   (Kp x Ke)
+//    (root entries of RU/RV are unused).
 //
 // Scratch of one product with r columns (compute type C), node-major:
 //  HODLR  PS[node][col][e], e < Ke: a leaf holds V^T X of its rows for every
@@ -54,13 +56,23 @@ struct MatView {
   const void* A_lo;     // lo plane (BF16X2) or nullptr
   const void* W;        // projection operand
   const void* W_lo;
-  const void* RU;       // HSS tree operators (compute type)
-  const void* RVt;
+  const void* RU;       // HSS tree operators (compute type), layouts above
+  const void* RV;
   const void* B12;
   const void* B21;
   int kk[kMaxDepth + 2];    // HODLR padded rank of level l (index 1..p)
   int koff[kMaxDepth + 2];  // HODLR offset of level l inside the Ke block
 };
+
+// Optional per-kernel event timing (phase 0 project, 1 tree upsweep, 2 HSS downsweep, 3 expand).
+struct Prof {
+  virtual void mark(int phase, bool start, cudaStream_t s) = 0;
+  virtual ~Prof() {}
+};
+
+inline void prof_mark(Prof* p, int phase, bool start, cudaStream_t s) {
+  if (p) p->mark(phase, start, s);
+}
 
 struct Scratch {
   void* PS;   // HODLR partial sums
@@ -69,21 +81,20 @@ struct Scratch {
   void* yf;
   int* cnt;
   int* err;   // device error word (bounded waits)
+  Prof* prof; // host-side timing hook or nullptr (never read by kernels)
 };
 
-// Launches the SIMT path (all storage types, any r).  Defined in k_simt_*.cu.
-hm_status launch_simt(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx,
-                      int xt, void* Y, int64_t ldy, int yt, cudaStream_t s);
-
-// Per-storage-type entry points of the SIMT path.
-hm_status launch_simt_f64(const MatView&, const Scratch&, int64_t, const void*, int64_t, int, void*,
-                          int64_t, int, cudaStream_t);
-hm_status launch_simt_f32(const MatView&, const Scratch&, int64_t, const void*, int64_t, int, void*,
-                          int64_t, int, cudaStream_t);
-hm_status launch_simt_bf16(const MatView&, const Scratch&, int64_t, const void*, int64_t, int, void*,
-                           int64_t, int, cudaStream_t);
-hm_status launch_simt_bf16x2(const MatView&, const Scratch&, int64_t, const void*, int64_t, int,
-                             void*, int64_t, int, cudaStream_t);
+// One phase of the SIMT path (0 projection, 1 tree upsweep / sums, 2 HSS
+// downsweep, 3 leaf expansion) for one storage type; `pdl` launches it with programmatic stream
+// serialization.  Defined in k_simt_<type>.cu.
+#define HM_SIMT_PHASE_DECL(T)                                                                       \
+  hm_status simt_phase_##T(int phase, const MatView& mv, const Scratch& ws, int64_t r, const void* X, \
+                           int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t s, bool pdl);
+HM_SIMT_PHASE_DECL(f64)
+HM_SIMT_PHASE_DECL(f32)
+HM_SIMT_PHASE_DECL(bf16)
+HM_SIMT_PHASE_DECL(bf16x2)
+#undef HM_SIMT_PHASE_DECL
 
 // Scratch element counts for r columns (in compute-type elements) and counter count.
 size_t scratch_elems(const MatView& mv, int64_t r);

@@ -3,9 +3,9 @@
 
 namespace hmi {
 
-hm_status launch_simt_bf16x2(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx,
-                        int xt, void* Y, int64_t ldy, int yt, cudaStream_t s) {
-  return launch_simt_t<HM_BF16X2>(mv, ws, r, X, ldx, xt, Y, ldy, yt, s);
+hm_status simt_phase_bf16x2(int phase, const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx,
+                      int xt, void* Y, int64_t ldy, int yt, cudaStream_t s, bool pdl) {
+  return simt_phase_t<HM_BF16X2>(phase, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
 }
 
 }  // namespace hmi

@@ -49,10 +49,14 @@ def bound_factor(storage, kind, p, acc_len, tensor_core=False):
     (HODLR: U, V, X and the staged T; HSS: U, V, X, y-hat and the 2(p-1) translations
     and the coupling) plus the accumulations."""
     u_s = UNIT[storage]
-    u_acc = 2.0 ** -53 if storage == "f64" else (2.0 ** -23 if tensor_core else 2.0 ** -24)
+    # Tensor-core accumulation is not assumed to round to nearest: one ulp of FP32.
+    u_acc = 2.0 ** -53 if storage == "f64" else (2.0 ** -23 if tensor_core or storage in ("bf16", "bf16x2")
+                                                else 2.0 ** -24)
     c_round = 5 if kind == "hodlr" else 2 * p + 6
     if storage != "f64":
         c_round += 2   # intermediates (T / x-hat / y-hat) held in float32
+    if storage in ("bf16", "bf16x2"):
+        c_round += 2   # the tensor-core path rounds X and Z to the storage format
     return c_round * u_s + OB.gamma(acc_len, u_acc)
 
 

@@ -286,3 +286,68 @@ def test_config_exp_kernel_n262144(storage, r):
         ref = OM.matmat_rows(c, g, Xe, rows)
         env = OB.envelope_rows(c, g, Xe, rows)
         H.check_bound(Y[rows], ref, env, fac, storage)
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core expansion (tcgen05) against the oracle and against the SIMT path
+# ---------------------------------------------------------------------------
+
+TC_CASES = [
+    ("hss_uniform_m256_r64", "hss", [256 * (i + 1) for i in range(16)], 32, 64),
+    ("hodlr_ragged_m144_r20", "hodlr", OT.default_leaf_ends(4600, 150), 6, 20),
+    ("hodlr_deep_K80_r128", "hodlr", OT.default_leaf_ends(8192, 256), 8, 128),
+    ("hss_ragged_r33", "hss", OT.default_leaf_ends(3001, 200), 16, 33),
+    ("hss_leaf512_r16", "hss", [512 * (i + 1) for i in range(4)], 24, 16),
+    ("hodlr_r300_chunks", "hodlr", OT.default_leaf_ends(2048, 256), 8, 300),
+    ("hss_empty_leaf_r48", "hss", [300, 600, 600, 900], 8, 48),
+]
+
+
+@pytest.mark.parametrize("storage", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("name,kind,c,k,r", TC_CASES)
+def test_tensor_core_expansion(storage, name, kind, c, k, r):
+    g = _gens(kind, c, 41, k)
+    n = int(c[-1])
+    X = H.exact_input(np.random.default_rng(r).standard_normal((n, r)), "f32")
+    A = hm.Matrix.create(hm.Tree.from_leaf_ends(c), g, storage)
+    Xd = H.to_dev(X, "f32")
+    A.set_path(2)                                   # tensor cores whenever supported
+    Yt = H.to_host(A.matmat(Xd, out_dtype=torch.float32))
+    A.set_path(1)                                   # SIMT only
+    Ys = H.to_host(A.matmat(Xd, out_dtype=torch.float32))
+    hm.device_status()
+    ref = OM.matmat(c, g, X)
+    info = A.info()
+    fac = H.bound_factor(storage, kind, info["depth"], H.acc_length(info, kind), tensor_core=True)
+    env = OB.envelope(c, g, X)
+    H.check_bound(Yt, ref, env, fac, name + " tensor cores")
+    H.check_bound(Ys, ref, env, fac, name + " simt")
+
+
+def test_tensor_core_split_f64_output_and_bf16_input():
+    c = OT.default_leaf_ends(2048, 256)
+    g = _gens("hss", c, 5, 16)
+    X = H.exact_input(np.random.default_rng(0).standard_normal((2048, 32)), "bf16")
+    A = hm.Matrix.create(hm.Tree.from_leaf_ends(c), g, "bf16x2")
+    A.set_path(2)
+    Y = H.to_host(A.matmat(H.to_dev(X, "bf16"), out_dtype=torch.float64))
+    ref = OM.matmat(c, g, X)
+    info = A.info()
+    H.check_bound(Y, ref, OB.envelope(c, g, X),
+                  H.bound_factor("bf16x2", "hss", info["depth"], H.acc_length(info, "hss"), True), "split f64 out")
+    assert H.col_rel_err(Y, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("storage", ["bf16", "bf16x2"])
+def test_tensor_core_deterministic_and_streams(storage):
+    c = OT.default_leaf_ends(16384, 256)
+    g = _gens("hss", c, 3, 32)
+    A = hm.Matrix.create(hm.Tree.from_leaf_ends(c), g, storage)
+    X = H.to_dev(np.random.default_rng(1).standard_normal((16384, 64)), "f32")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        Y1 = A.matmat(X)
+        Y2 = A.matmat(X)
+    s.synchronize()
+    assert torch.equal(Y1, Y2)
+    hm.device_status()
