@@ -190,6 +190,29 @@ hm_status hm_hodlr_matmat(const hm_matrix* A, int64_t r, const void* X, int64_t 
 hm_status hm_hss_matmat(const hm_matrix* A, int64_t r, const void* X, int64_t ldx, hm_dtype xt,
                         void* Y, int64_t ldy, hm_dtype yt, void* stream);
 
+/* Y = A X like hm_hodlr_matmat / hm_hss_matmat (chosen by the matrix's
+ * kind), but allocating nothing.  This entry point has no counterpart in the
+ * paper; it exists for callers that cannot allocate device memory where they
+ * need a product: code recorded into a CUDA graph (allocation is not allowed
+ * during stream capture), latency-bound serving loops that must not stall on
+ * cudaMalloc's implicit device synchronisation, and applications whose own
+ * allocator owns all device memory.
+ *   - The per-call scratch lives in one fixed 8 MiB device array compiled into
+ *     the library (every GPU that loads the library holds it until the process
+ *     exits).  A product whose scratch would exceed 8 MiB -- about
+ *     (2L-1) * r * (rank terms) * 4 bytes, see hm_matrix_info -- is rejected
+ *     with HM_EINVAL and a message naming the limit; split the columns of X.
+ *   - X and Y must be device memory (host buffers would need staging memory).
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - Every call shares the array and it keeps the previous call's contents;
+ *     the call clears what must start at zero on `stream`.  Calls whose
+ *     kernels overlap on the GPU (concurrent streams or host threads) race on
+ *     it and must be serialised by the caller.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called. */
+hm_status hm_matmat_noalloc(const hm_matrix* A, int64_t r, const void* X, int64_t ldx, hm_dtype xt,
+                            void* Y, int64_t ldy, hm_dtype yt, void* stream);
+
 /* Waits for `stream` and reports whether a device-side bounded wait of this
  * library timed out since the last call (HM_ETIMEOUT), then clears the flag. */
 hm_status hm_device_status(void* stream);

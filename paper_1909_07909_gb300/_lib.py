@@ -70,6 +70,7 @@ _decl("hm_matrix_set_path", C.c_int, vp, C.c_int32)
 _decl("hm_hodlr_matmat", C.c_int, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_int, vp)
 _decl("hm_hss_matmat", C.c_int, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_int, vp)
 _decl("hm_device_status", C.c_int, vp)
+_decl("hm_matmat_noalloc", C.c_int, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_int, vp)
 _decl("hm_matrix_profile", C.c_int, vp, C.c_int32)
 _decl("hm_matrix_phase_times", C.c_int, vp, C.POINTER(C.c_double), C.POINTER(C.c_int64))
 _decl("hm_destroy", None, vp)
