@@ -46,6 +46,12 @@ class hm_matrix_info_t(C.Structure):
                 ("device_bytes", C.c_size_t)]
 
 
+class hm_batch_info_t(C.Structure):
+    _fields_ = [("count", C.c_int32), ("launches_per_run", C.c_int32), ("items", C.c_int64 * 5),
+                ("grid", C.c_int32 * 5), ("graph", C.c_int32), ("tuned", C.c_int32), ("grid_mult", C.c_int32),
+                ("rc_cap", C.c_int32), ("rct_cap", C.c_int32), ("tile_rows", C.c_int32)]
+
+
 def _decl(name, res, *args):
     f = getattr(lib, name)
     f.restype = res
@@ -73,6 +79,10 @@ _decl("hm_device_status", C.c_int, vp)
 _decl("hm_matmat_noalloc", C.c_int, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_int, vp)
 _decl("hm_matrix_profile", C.c_int, vp, C.c_int32)
 _decl("hm_matrix_phase_times", C.c_int, vp, C.POINTER(C.c_double), C.POINTER(C.c_int64))
+_decl("hm_batch_create", C.c_int, C.POINTER(vp), C.POINTER(C.c_int64), C.c_int32, C.POINTER(vp))
+_decl("hm_batch_tune", C.c_int, vp, C.c_char_p)
+_decl("hm_batch_run", C.c_int, vp, C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int, vp)
+_decl("hm_batch_info", C.c_int, vp, C.POINTER(hm_batch_info_t))
 _decl("hm_destroy", None, vp)
 
 

@@ -222,6 +222,47 @@ class Matrix:
             self._h = None
 
 
+class Batch:
+    """Many products Y_j = A_j X_j run as one persistent launch per phase."""
+
+    def __init__(self, mats, rs):
+        self.mats = list(mats)
+        self.rs = [int(v) for v in rs]
+        hs = (vp * len(self.mats))(*[m._h for m in self.mats])
+        rr = (C.c_int64 * len(self.rs))(*self.rs)
+        h = vp()
+        check(lib.hm_batch_create(hs, rr, len(self.mats), C.byref(h)), "hm_batch_create")
+        self._h = h
+
+    def tune(self, cache_path=None):
+        check(lib.hm_batch_tune(self._h, cache_path.encode() if cache_path else None), "hm_batch_tune")
+
+    def run(self, Xs, Ys, xt=L.HM_F32, yt=L.HM_F32, stream=None):
+        """Xs, Ys: sequences of device pointers (ints) or column-major tensors."""
+        xp = [x.data_ptr() if hasattr(x, "data_ptr") else int(x) for x in Xs]
+        yp = [y.data_ptr() if hasattr(y, "data_ptr") else int(y) for y in Ys]
+        xa = (vp * len(xp))(*xp)
+        ya = (vp * len(yp))(*yp)
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        check(lib.hm_batch_run(self._h, xa, ya, _dtype_code(xt), _dtype_code(yt), vp(stream) if stream else None),
+              "hm_batch_run")
+
+    def info(self):
+        inf = L.hm_batch_info_t()
+        check(lib.hm_batch_info(self._h, C.byref(inf)), "hm_batch_info")
+        out = {f: getattr(inf, f) for f, _ in L.hm_batch_info_t._fields_}
+        out["items"] = list(out["items"])
+        out["grid"] = list(out["grid"])
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.hm_destroy(h)
+            self._h = None
+
+
 def colmajor(t):
     """Column-major copy of a 2-D torch tensor (layout helper for callers)."""
     return t.t().contiguous().t()

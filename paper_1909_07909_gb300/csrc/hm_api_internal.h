@@ -108,10 +108,15 @@ hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int
 // Tensor-core expansion (k_tc.cu).
 void make_tensor_maps(hm_matrix* A);
 bool use_tensor_cores(const hm_matrix* A, int64_t r);
+// Shape of the tensor-core expansion of A for r columns (false if none fits).
+bool tc_plan(const hm_matrix* A, int64_t r, int* nt, int* nK, int* nX, int* nst, int* tiles);
+size_t tc_tile_smem(bool split, int NT, int nK, int nst);
+int tc_tile_ncols(bool split, int NT);
 hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                            int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl);
 
 // Releases batch and server objects (defined with them).
 void destroy_other(void* any, uint32_t magic);
+void destroy_server(void* any);
 
 }  // namespace hmi

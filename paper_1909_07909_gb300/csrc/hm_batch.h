@@ -1,0 +1,54 @@
+// Batched products: many matrices of uneven size, rank, storage and number of
+// right-hand sides run through one persistent launch per phase (projection,
+// tree upsweep, HSS downsweep, SIMT expansion, tensor-core expansion).
+//
+// Each product keeps exactly the blocking it would have on its own (column
+// chunks, tree step spans, tiles), so a product's result is bit-identical in
+// a batch and alone; the batch only changes which block runs it and when.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda.h>
+
+#include "hm_internal.h"
+
+namespace hmi {
+
+// One product of the batch, as the kernels see it (device memory).
+struct BatchJob {
+  MatView mv;
+  Scratch ws;
+  int64_t r;
+  int storage;
+  int rc_p, rc_e;      // SIMT column chunks: projection, expansion
+  int rct;             // tree column chunk
+  int g, s0;           // tree upsweep: step span, first-step span
+  int s_lvl, G;        // downsweep: subtree level, chain prefetch depth
+  int RT, tiles;       // SIMT expansion: rows per tile, tiles per leaf
+  int tc;              // 1: tensor-core expansion
+  int nt, split, nK, nX, nst, tc_tiles;
+};
+
+// Per-run inputs and outputs of one product.
+struct BatchIO {
+  const void* X;
+  void* Y;
+  int64_t ldx, ldy;
+  int xt, yt;
+};
+
+// One unit of work: product `job`, block coordinates (bx, by) of that
+// product's own launch of the phase.
+struct BItem {
+  int job, bx, by;
+};
+
+enum { BP_PROJECT = 0, BP_UP = 1, BP_DOWN = 2, BP_EXPAND = 3, BP_EXPAND_TC = 4, BP_COUNT = 5 };
+
+cudaError_t batch_launch_simt(int phase, const BatchJob* jobs, const BatchIO* io, const BItem* items, int n,
+                              int grid, size_t smem, cudaStream_t st, bool pdl);
+cudaError_t batch_launch_tc(const BatchJob* jobs, const BatchIO* io, const CUtensorMap* maps, const BItem* items,
+                            int n, int grid, size_t smem, int ncol, cudaStream_t st, bool pdl);
+
+}  // namespace hmi

@@ -395,15 +395,12 @@ __host__ __device__ inline int up_smem_elems(bool hss, int rc, int Kp, int Ke, i
 }
 
 template <typename C, int RC>
-__global__ void __launch_bounds__(256) k_tree_up(MatView mv, Scratch ws, int64_t r, int g, int nchunks) {
-  pdl_launch_dependents();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
+__device__ void tree_up_block(const MatView& mv, const Scratch& ws, int64_t r, int g, int nchunks, int bx,
+                              int chunk, C* sm) {
   __shared__ int s_last;
   const bool hss = (mv.kind == HM_HSS);
   const int Kp = mv.Kp, Ke = mv.Ke;
   const int K = hss ? Kp : Ke;
-  const int chunk = blockIdx.y;
   const int col0 = chunk * RC;
   const int ncols = min(static_cast<int64_t>(RC), r - col0);
   const int lmin = hss ? 0 : 1;
@@ -411,7 +408,7 @@ __global__ void __launch_bounds__(256) k_tree_up(MatView mv, Scratch ws, int64_t
   C* data = static_cast<C*>(hss ? ws.xh : ws.PS);
   C* yc = static_cast<C*>(ws.yc);
   int lc = mv.p;
-  int pos = static_cast<int>(blockIdx.x) << min(g, mv.p - lmin);
+  int pos = bx << min(g, mv.p - lmin);
   bool first = true;
   pdl_wait();   // the leaves' projections come from the projection kernel
   while (lc > lmin) {
@@ -514,15 +511,17 @@ __global__ void __launch_bounds__(256) k_tree_up(MatView mv, Scratch ws, int64_t
   }
 }
 
-template <int S, int RC, int TR>
-__global__ void __launch_bounds__(256, 2) k_project(MatView mv, Scratch ws, int64_t r, const void* X,
-                                                 int64_t ldx, int xt, int nchunks) {
-  using C = typename Stor<S>::C;
+template <typename C, int RC>
+__global__ void __launch_bounds__(256) k_tree_up(MatView mv, Scratch ws, int64_t r, int g, int nchunks) {
   pdl_launch_dependents();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int leaf = blockIdx.x;
-  const int chunk = blockIdx.y;
+  tree_up_block<C, RC>(mv, ws, r, g, nchunks, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
+}
+
+template <int S, int RC, int TR>
+__device__ void project_block(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx, int xt,
+                              int leaf, int chunk, typename Stor<S>::C* sm) {
+  using C = typename Stor<S>::C;
   const int col0 = chunk * RC;
   const int ncols = min(static_cast<int64_t>(RC), r - col0);
   const int64_t a0 = mv.off[leaf];
@@ -549,6 +548,16 @@ __global__ void __launch_bounds__(256, 2) k_project(MatView mv, Scratch ws, int6
   }
 }
 
+template <int S, int RC, int TR>
+__global__ void __launch_bounds__(256, 2) k_project(MatView mv, Scratch ws, int64_t r, const void* X,
+                                                 int64_t ldx, int xt, int nchunks) {
+  using C = typename Stor<S>::C;
+  pdl_launch_dependents();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  (void)nchunks;
+  project_block<S, RC, TR>(mv, ws, r, X, ldx, xt, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
+}
+
 // Shared-memory elements of the downsweep: the subtree part needs, per level
 // of a depth-d subtree, 2^d operator halves and two y buffers of 2^d nodes;
 // the chain part prefetches G levels (operator half + coupling block) at once.
@@ -559,15 +568,12 @@ __host__ __device__ inline int down_smem_elems(int rc, int Ke, int d, int G) {
 }
 
 template <typename C, int RC>
-__global__ void __launch_bounds__(256) k_hss_down(MatView mv, Scratch ws, int64_t r, int s_lvl, int G) {
-  pdl_launch_dependents();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void down_block(const MatView& mv, const Scratch& ws, int64_t r, int s_lvl, int G, int pos, int chunk,
+                           unsigned char* smem_raw) {
   const int Ke = mv.Ke;
   const int d = mv.p - s_lvl;               // subtree depth
-  const int chunk = blockIdx.y;
   const int col0 = chunk * RC;
   const int ncols = min(static_cast<int64_t>(RC), r - col0);
-  const int pos = blockIdx.x;
   const C* RU = static_cast<const C*>(mv.RU);
   pdl_wait();                               // couplings come from the projection kernel
   const C* yc = static_cast<const C*>(ws.yc);
@@ -699,6 +705,13 @@ __global__ void __launch_bounds__(256) k_hss_down(MatView mv, Scratch ws, int64_
   }
 }
 
+template <typename C, int RC>
+__global__ void __launch_bounds__(256) k_hss_down(MatView mv, Scratch ws, int64_t r, int s_lvl, int G) {
+  pdl_launch_dependents();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  down_block<C, RC>(mv, ws, r, s_lvl, G, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 template <typename C>
 __device__ __forceinline__ C z_value(const MatView& mv, const Scratch& ws, int64_t r, int leaf, int e,
                                      int64_t col) {
@@ -718,15 +731,10 @@ __device__ __forceinline__ C z_value(const MatView& mv, const Scratch& ws, int64
 }
 
 template <int S, int RC, int TR>
-__global__ void __launch_bounds__(256) k_expand(MatView mv, Scratch ws, int64_t r, const void* X,
-                                                int64_t ldx, int xt, void* Y, int64_t ldy, int yt,
-                                                int RT, int tiles_per_leaf) {
+__device__ void expand_block(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx, int xt,
+                             void* Y, int64_t ldy, int yt, int RT, int leaf, int tile, int chunk,
+                             typename Stor<S>::C* sm) {
   using C = typename Stor<S>::C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int leaf = blockIdx.x / tiles_per_leaf;
-  const int tile = blockIdx.x % tiles_per_leaf;
-  const int chunk = blockIdx.y;
   const int col0 = chunk * RC;
   const int ncols = min(static_cast<int64_t>(RC), r - col0);
   const int64_t a0 = mv.off[leaf];
@@ -753,6 +761,16 @@ __global__ void __launch_bounds__(256) k_expand(MatView mv, Scratch ws, int64_t 
     const int c = idx / nrows, t = idx % nrows;
     store_y<C>(Y, yt, (a0 + t0 + t) + static_cast<int64_t>(col0 + c) * ldy, Os[c * OS + t]);
   }
+}
+
+template <int S, int RC, int TR>
+__global__ void __launch_bounds__(256) k_expand(MatView mv, Scratch ws, int64_t r, const void* X,
+                                                int64_t ldx, int xt, void* Y, int64_t ldy, int yt,
+                                                int RT, int tiles_per_leaf) {
+  using C = typename Stor<S>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  expand_block<S, RC, TR>(mv, ws, r, X, ldx, xt, Y, ldy, yt, RT, blockIdx.x / tiles_per_leaf,
+                          blockIdx.x % tiles_per_leaf, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
