@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-leaves", type=int, default=6, help="leaf row blocks in the CPU sample")
+    ap.add_argument("--workload", default="hss", choices=["hss", "batched", "serve"],
+                    help="hss: the HSS n=65536 headline; batched: 512 uneven matrices; serve: Poisson requests")
+    ap.add_argument("--count", type=int, default=0, help="matrices in the batched / serving workload")
+    ap.add_argument("--rates", default="1000,5000,10000,20000,50000")
+    ap.add_argument("--seconds", type=float, default=1.0, help="arrival window per rate (serve)")
     return ap.parse_args()
 
 
@@ -330,11 +335,193 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: 512 matrices, n log-uniform in [1024, 32768], rank in
+# {4, 8, 16, 32, 64}, 1..32 right-hand sides, half HODLR and half HSS.
+# ---------------------------------------------------------------------------
+
+def run_batched(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_1909_07909_gb300 as hm
+    torch.cuda.set_device(0)
+    rng = W.rng_for(4)
+    count = args.count or 512
+    spec = W.batch_spec(rng, count=count)
+    out = {"metric": METRIC, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+           "config": {"workload": "batched %d matrices, n log-uniform [1024,32768], rank {4..64}, r 1..32, "
+                                  "half HODLR/HSS, leaf 256" % count}}
+    res = {}
+    allm = {"bf16": [], "f32": [], "f64": []}
+    rs = []
+    for sp in spec:
+        tree = hm.Tree.default(sp["n"], 256)
+        c = tree.leaf_ends
+        g = (W.random_hodlr(rng, c, sp["k"]) if sp["kind"] == "hodlr" else W.random_hss(rng, c, sp["k"]))
+        for stg in allm:
+            allm[stg].append(hm.Matrix.create(tree, g, stg))
+        rs.append(sp["r"])
+        del g
+    for storage in ("bf16", "f32", "f64"):
+        mats = allm[storage]
+        td = torch.float64 if storage == "f64" else torch.float32
+        Xs = [torch.randn((sp["r"], sp["n"]), dtype=td, device="cuda").t() for sp in spec]
+        Ys = [torch.empty((sp["r"], sp["n"]), dtype=td, device="cuda").t() for sp in spec]
+        gen_bytes = sum(A.generator_bytes() for A in mats)
+        es = 8 if storage == "f64" else 4
+        io_bytes = sum(sp["n"] * sp["r"] * 2 * es for sp in spec)
+        step_bytes = gen_bytes + io_bytes
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        entry = {"bytes_per_run": step_bytes}
+        if storage != "f64":
+            B = hm.Batch(mats, rs)
+            t0 = time.perf_counter()
+            B.tune(None)
+            entry["tune_s"] = time.perf_counter() - t0
+            info = B.info()
+            for _ in range(args.warmup):
+                B.run(Xs, Ys)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(args.steps):
+                B.run(Xs, Ys)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            entry.update({"batched_ms": ms, "batched_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                          "launches_per_run": info["launches_per_run"], "graph": info["graph"],
+                          "tuned": {k: info[k] for k in ("grid_mult", "rc_cap", "rct_cap", "tile_rows")}})
+        loops = max(1, args.steps // 4)
+        for _ in range(2):
+            for A, X, Y in zip(mats, Xs, Ys):
+                A.matmat(X, Y)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(loops):
+            for A, X, Y in zip(mats, Xs, Ys):
+                A.matmat(X, Y)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / loops
+        entry.update({"loop_ms": ms, "loop_gbs": step_bytes / (ms * 1e-3) / 1e9})
+        res[storage] = entry
+        del Xs, Ys
+        allm[storage] = []
+        del mats
+        torch.cuda.empty_cache()
+    out["value"] = res["bf16"]["batched_gbs"]
+    out["ms_per_step"] = res["bf16"]["batched_ms"]
+    out["dtype"] = "bf16"
+    out["variants"] = res
+    out["batched_vs_fp64_unbatched"] = res["bf16"]["batched_gbs"] / res["f64"]["loop_gbs"]
+    out["gpu_launches"] = res["bf16"]["launches_per_run"] * args.steps
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Serving workload: 64 resident HSS matrices (n = 2^12..2^18, rank 16..64,
+# BF16), Poisson arrivals, 1..16 right-hand sides per request.
+# ---------------------------------------------------------------------------
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_1909_07909_gb300 as hm
+    torch.cuda.set_device(0)
+    rng = W.rng_for(5)
+    count = args.count or 64
+    spec = W.serve_spec(rng, count=count)
+    server = hm.Server(100 << 30, 4096)
+    mats, ids, pools = [], [], []
+    for sp in spec:
+        tree = hm.Tree.default(sp["n"], 256)
+        g = W.random_hss(rng, tree.leaf_ends, sp["k"])
+        A = hm.Matrix.create(tree, g, "bf16")
+        del g
+        mats.append(A)
+        ids.append(server.register(A))
+        X = torch.randn((16, sp["n"]), dtype=torch.float32, device="cuda").t()
+        Ys = [torch.empty((16, sp["n"]), dtype=torch.float32, device="cuda").t() for _ in range(48)]
+        pools.append((X, Ys))
+    torch.cuda.synchronize()
+    rates = [int(v) for v in args.rates.split(",") if v]
+    by_rate = {}
+    for rate in rates:
+        nreq = max(50, int(rate * args.seconds))
+        gaps = rng.exponential(1.0 / rate, size=nreq)
+        which = rng.integers(0, count, size=nreq)
+        rr = rng.integers(1, 17, size=nreq)
+        server.reset_stats()
+        tickets = []
+        busy = 0
+        t0 = time.perf_counter()
+        due = t0
+        slot = [0] * count
+        for q in range(nreq):
+            due += gaps[q]
+            while time.perf_counter() < due:
+                pass
+            j = int(which[q])
+            X, Ys = pools[j]
+            Y = Ys[slot[j] % len(Ys)]
+            slot[j] += 1
+            t = server.submit(ids[j], int(rr[q]), X.data_ptr(), Y.data_ptr())
+            if t is None:
+                busy += 1
+            else:
+                tickets.append(t)
+            if len(tickets) > 2048:
+                server.wait(tickets.pop(0), 60000)
+        for t in tickets:
+            server.wait(t, 60000)
+        wall = time.perf_counter() - t0
+        stt = server.stats()
+        by_rate[str(rate)] = {"offered_rps": rate, "requests": nreq, "refused": busy,
+                              "p50_ms": stt["p50_us"] / 1e3, "p99_ms": stt["p99_us"] / 1e3,
+                              "throughput_rps": stt["throughput_rps"], "gbs": stt["gbs"],
+                              "launches": stt["launches"], "max_merged": stt["max_merged"], "wall_s": wall}
+    # FP64 unbatched reference on the same GPU: each request alone, one after another
+    f64 = []
+    for j in range(min(count, 8)):
+        tree = mats[j].tree
+        g = W.random_hss(W.rng_for(5, 100 + j), tree.leaf_ends, spec[j]["k"])
+        A64 = hm.Matrix.create(tree, g, "f64")
+        X = torch.randn((8, spec[j]["n"]), dtype=torch.float64, device="cuda").t()
+        A64.matmat(X)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            A64.matmat(X)
+        torch.cuda.synchronize()
+        f64.append((time.perf_counter() - t0) / 5)
+    f64_ms = 1e3 * float(np.mean(f64))
+    top = by_rate[str(max(rates))]
+    out = {"metric": METRIC, "value": top["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "steps": len(rates),
+           "warmup": 0, "ms_per_step": top["p50_ms"], "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": "serving %d resident HSS matrices n=2^12..2^18 rank 16..64 BF16, Poisson "
+                                  "arrivals, 1..16 RHS per request, 100 GB budget" % count},
+           "by_rate": by_rate, "fp64_unbatched_ms_per_request_r8": f64_ms,
+           "resident_bytes": server.stats()["resident_bytes"]}
+    server.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     rank, local, world = dist_env()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args) if rank == 0 else 0
+    if args.workload == "serve":
+        return run_serve(args) if rank == 0 else 0
     os.environ.setdefault("OPENBLAS_NUM_THREADS", str(os.cpu_count()))
     import numpy as np
     import torch

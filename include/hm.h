@@ -281,6 +281,59 @@ hm_status hm_batch_run(hm_batch* b, const void* const* X, void* const* Y, hm_dty
 
 hm_status hm_batch_info(const hm_batch* b, hm_batch_info_t* out);
 
+/* ---------------------------------------------------------------------- */
+/* Serving (continuous batching of product requests; not in the paper)    */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t submitted;        /* requests offered to hm_serve_submit */
+  int64_t admitted;         /* accepted */
+  int64_t rejected;         /* refused with HM_EBUSY */
+  int64_t completed;        /* finished */
+  int64_t launches;         /* merged products launched */
+  int32_t pending;          /* admitted and not yet completed */
+  int32_t max_merged;       /* most requests merged into one product */
+  size_t resident_bytes;    /* device bytes of registered matrices and their buffers */
+  double p50_us;            /* submit-to-completion latency percentiles and mean, */
+  double p99_us;            /*   over completed requests since creation or reset */
+  double mean_us;
+  double throughput_rps;    /* completed requests per second (first submit to last completion) */
+  double gbs;               /* algorithmic bytes of the launched products per second */
+} hm_serve_stats_t;
+
+/* Creates a server on the current device: at most max_slots requests may be
+ * admitted and unfinished at once, and registered matrices plus admitted
+ * requests' buffers may use at most mem_budget device bytes.  A worker thread
+ * takes the queued requests continuously, merges requests for the same matrix
+ * into one product with up to 64 columns, and runs products of different
+ * matrices on separate streams so they overlap. */
+hm_status hm_serve_create(size_t mem_budget, int32_t max_slots, hm_server** out);
+
+/* Makes a matrix resident for serving (F32, BF16 or BF16X2 storage).  Its
+ * scratch and merge buffers are reserved now and counted, with the matrix
+ * itself, against the budget (HM_ENOMEM if they do not fit).  The matrix's
+ * kernel family is fixed (tensor cores for BF16/BF16X2, SIMT otherwise) so
+ * that a request's result does not depend on the requests it is merged with.
+ * The matrix must outlive the server.  *id receives the matrix's id. */
+hm_status hm_serve_register(hm_server* s, hm_matrix* A, int32_t* id);
+
+/* Queues Y = A_id X for X, Y device buffers of n x r float32 values,
+ * column-major with leading dimension n (1 <= r <= 64).  Non-blocking:
+ * returns HM_EBUSY, without queuing, when no slot or budget is free.  *ticket
+ * identifies the request for hm_serve_wait / hm_serve_poll. */
+hm_status hm_serve_submit(hm_server* s, int32_t id, int64_t r, const void* X, void* Y, uint64_t* ticket);
+
+/* Waits up to timeout_ms for a request: HM_OK (Y is written), HM_ETIMEOUT
+ * (still pending; the ticket stays valid) or the error of its product.  Never
+ * waits longer than the timeout. */
+hm_status hm_serve_wait(hm_server* s, uint64_t ticket, int32_t timeout_ms);
+
+/* Non-blocking: HM_OK when the request has finished, HM_EBUSY while pending. */
+hm_status hm_serve_poll(hm_server* s, uint64_t ticket);
+
+hm_status hm_serve_stats(hm_server* s, hm_serve_stats_t* out);
+hm_status hm_serve_reset_stats(hm_server* s);
+
 /* Releases any object created by this library (tree, matrix, batch, server).
  * NULL-safe.  A matrix registered with a server must be released after the
  * server. */

@@ -6,7 +6,7 @@ Python binding of libhm (include/hm.h).  The library must be built first
 
 from ._lib import (HM_BF16, HM_BF16X2, HM_F32, HM_F64, HM_HODLR, HM_HSS, HMError,  # noqa: F401
                    LIB_PATH, lib)
-from .api import Batch, Matrix, Tree, colmajor, device_status  # noqa: F401
+from .api import Batch, Matrix, Server, Tree, colmajor, device_status  # noqa: F401
 
-__all__ = ["Tree", "Matrix", "Batch", "colmajor", "device_status", "HMError", "lib", "LIB_PATH",
+__all__ = ["Tree", "Matrix", "Batch", "Server", "colmajor", "device_status", "HMError", "lib", "LIB_PATH",
            "HM_F64", "HM_F32", "HM_BF16", "HM_BF16X2", "HM_HODLR", "HM_HSS"]

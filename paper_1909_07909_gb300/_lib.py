@@ -52,6 +52,14 @@ class hm_batch_info_t(C.Structure):
                 ("rc_cap", C.c_int32), ("rct_cap", C.c_int32), ("tile_rows", C.c_int32)]
 
 
+class hm_serve_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("rejected", C.c_int64),
+                ("completed", C.c_int64), ("launches", C.c_int64), ("pending", C.c_int32),
+                ("max_merged", C.c_int32), ("resident_bytes", C.c_size_t), ("p50_us", C.c_double),
+                ("p99_us", C.c_double), ("mean_us", C.c_double), ("throughput_rps", C.c_double),
+                ("gbs", C.c_double)]
+
+
 def _decl(name, res, *args):
     f = getattr(lib, name)
     f.restype = res
@@ -83,6 +91,13 @@ _decl("hm_batch_create", C.c_int, C.POINTER(vp), C.POINTER(C.c_int64), C.c_int32
 _decl("hm_batch_tune", C.c_int, vp, C.c_char_p)
 _decl("hm_batch_run", C.c_int, vp, C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int, vp)
 _decl("hm_batch_info", C.c_int, vp, C.POINTER(hm_batch_info_t))
+_decl("hm_serve_create", C.c_int, C.c_size_t, C.c_int32, C.POINTER(vp))
+_decl("hm_serve_register", C.c_int, vp, vp, C.POINTER(C.c_int32))
+_decl("hm_serve_submit", C.c_int, vp, C.c_int32, C.c_int64, vp, vp, C.POINTER(C.c_uint64))
+_decl("hm_serve_wait", C.c_int, vp, C.c_uint64, C.c_int32)
+_decl("hm_serve_poll", C.c_int, vp, C.c_uint64)
+_decl("hm_serve_stats", C.c_int, vp, C.POINTER(hm_serve_stats_t))
+_decl("hm_serve_reset_stats", C.c_int, vp)
 _decl("hm_destroy", None, vp)
 
 

@@ -263,6 +263,58 @@ class Batch:
             self._h = None
 
 
+class Server:
+    """Resident matrices and continuously batched product requests."""
+
+    def __init__(self, mem_budget, max_slots):
+        h = vp()
+        check(lib.hm_serve_create(int(mem_budget), int(max_slots), C.byref(h)), "hm_serve_create")
+        self._h = h
+        self.mats = []
+
+    def register(self, A):
+        i = C.c_int32()
+        check(lib.hm_serve_register(self._h, A._h, C.byref(i)), "hm_serve_register")
+        self.mats.append(A)
+        return i.value
+
+    def submit(self, mid, r, X, Y):
+        """Returns a ticket, or None when the server refuses (HM_EBUSY)."""
+        t = C.c_uint64()
+        st = lib.hm_serve_submit(self._h, int(mid), int(r), vp(X), vp(Y), C.byref(t))
+        if st == L.HM_EBUSY:
+            return None
+        check(st, "hm_serve_submit")
+        return t.value
+
+    def wait(self, ticket, timeout_ms=10000):
+        return check(lib.hm_serve_wait(self._h, int(ticket), int(timeout_ms)), "hm_serve_wait")
+
+    def poll(self, ticket):
+        st = lib.hm_serve_poll(self._h, int(ticket))
+        if st == L.HM_EBUSY:
+            return False
+        check(st, "hm_serve_poll")
+        return True
+
+    def stats(self):
+        sst = L.hm_serve_stats_t()
+        check(lib.hm_serve_stats(self._h, C.byref(sst)), "hm_serve_stats")
+        return {f: getattr(sst, f) for f, _ in L.hm_serve_stats_t._fields_}
+
+    def reset_stats(self):
+        check(lib.hm_serve_reset_stats(self._h), "hm_serve_reset_stats")
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.hm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
 def colmajor(t):
     """Column-major copy of a 2-D torch tensor (layout helper for callers)."""
     return t.t().contiguous().t()
