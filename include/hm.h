@@ -252,6 +252,7 @@ typedef struct {
   int32_t rc_cap;            /*   widest SIMT column chunk, */
   int32_t rct_cap;           /*   widest tree column chunk, */
   int32_t tile_rows;         /*   rows per SIMT expansion tile */
+  int32_t capture_error;     /* CUDA error that prevented graph capture (runs then launch directly), 0 if none */
 } hm_batch_info_t;
 
 /* Groups `count` products Y_j = A_j X_j (r[j] right-hand sides each) into one

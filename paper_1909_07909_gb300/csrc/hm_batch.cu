@@ -61,6 +61,7 @@ struct hm_batch {
   std::vector<hmi::BatchIO> h_io;
   cudaGraphExec_t gexec = nullptr;
   bool use_graph = true;
+  int capture_error = 0;   // CUDA error of a failed capture (0 if none)
   int tuned = 0;
 };
 
@@ -185,6 +186,11 @@ static hm_status build_plan(hm_batch* b) {
     if (p != BP_EXPAND_TC && b->smem[p] > 0) per_sm = std::max(1, std::min(per_sm, static_cast<int>((228 * 1024) / (b->smem[p] + 1024))));
     b->grid[p] = std::max(0, std::min(n, b->sms * per_sm));
   }
+  for (int p = 0; p < BP_COUNT; ++p) {
+    if (b->items[p].empty()) continue;
+    if (p == BP_EXPAND_TC) batch_set_smem_tc(b->smem[p]);
+    else batch_set_smem(p, b->smem[p]);
+  }
   // upload
   cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(BatchJob) * std::max(b->count, 1));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_jobs, b->jobs.data(), sizeof(BatchJob) * b->count, cudaMemcpyHostToDevice);
@@ -236,6 +242,7 @@ static hm_status capture(hm_batch* b, cudaStream_t s) {
   (void)s;
   if (e != cudaSuccess || e2 != cudaSuccess || st != HM_OK || !graph) {
     if (graph) cudaGraphDestroy(graph);
+    b->capture_error = (e != cudaSuccess) ? e : (e2 != cudaSuccess ? e2 : -1);
     cudaGetLastError();
     b->use_graph = false;  // fall back to direct launches of the same kernels
     return HM_OK;
@@ -243,6 +250,7 @@ static hm_status capture(hm_batch* b, cudaStream_t s) {
   e = cudaGraphInstantiate(&b->gexec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
+    b->capture_error = 1000 + e;
     cudaGetLastError();
     b->gexec = nullptr;
     b->use_graph = false;
@@ -497,6 +505,7 @@ extern "C" hm_status hm_batch_info(const hm_batch* b, hm_batch_info_t* out) {
   }
   out->launches_per_run = launches;
   out->graph = (b->use_graph && b->gexec) ? 1 : 0;
+  out->capture_error = b->capture_error;
   out->tuned = b->tuned;
   out->grid_mult = b->knobs.grid_mult;
   out->rc_cap = b->knobs.rc_cap;

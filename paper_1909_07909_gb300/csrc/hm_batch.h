@@ -46,6 +46,10 @@ struct BItem {
 
 enum { BP_PROJECT = 0, BP_UP = 1, BP_DOWN = 2, BP_EXPAND = 3, BP_EXPAND_TC = 4, BP_COUNT = 5 };
 
+// Shared-memory attributes are set when a plan is built, so launches can be
+// recorded into a CUDA graph.
+void batch_set_smem(int phase, size_t smem);
+void batch_set_smem_tc(size_t smem);
 cudaError_t batch_launch_simt(int phase, const BatchJob* jobs, const BatchIO* io, const BItem* items, int n,
                               int grid, size_t smem, cudaStream_t st, bool pdl);
 cudaError_t batch_launch_tc(const BatchJob* jobs, const BatchIO* io, const CUtensorMap* maps, const BItem* items,

@@ -95,23 +95,27 @@ __global__ void __launch_bounds__(256) k_batch_simt(const BatchJob* jobs, const 
   }
 }
 
+void batch_set_smem(int phase, size_t smem) {
+  const int v = static_cast<int>(smem);
+  switch (phase) {
+    case BP_PROJECT: cudaFuncSetAttribute(k_batch_simt<BP_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+    case BP_UP: cudaFuncSetAttribute(k_batch_simt<BP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+    case BP_DOWN: cudaFuncSetAttribute(k_batch_simt<BP_DOWN>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+    default: cudaFuncSetAttribute(k_batch_simt<BP_EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+  }
+}
+
+// Launch only (no attribute calls, so it can be recorded into a CUDA graph).
 cudaError_t batch_launch_simt(int phase, const BatchJob* jobs, const BatchIO* io, const BItem* items, int n,
                               int grid, size_t smem, cudaStream_t st, bool pdl) {
   switch (phase) {
     case BP_PROJECT:
-      cudaFuncSetAttribute(k_batch_simt<BP_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
       return launch_k(k_batch_simt<BP_PROJECT>, dim3(grid), dim3(256), smem, st, pdl, jobs, io, items, n);
     case BP_UP:
-      cudaFuncSetAttribute(k_batch_simt<BP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
       return launch_k(k_batch_simt<BP_UP>, dim3(grid), dim3(256), smem, st, pdl, jobs, io, items, n);
     case BP_DOWN:
-      cudaFuncSetAttribute(k_batch_simt<BP_DOWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
       return launch_k(k_batch_simt<BP_DOWN>, dim3(grid), dim3(256), smem, st, pdl, jobs, io, items, n);
     default:
-      cudaFuncSetAttribute(k_batch_simt<BP_EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
       return launch_k(k_batch_simt<BP_EXPAND>, dim3(grid), dim3(256), smem, st, pdl, jobs, io, items, n);
   }
 }

@@ -57,9 +57,12 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+void batch_set_smem_tc(size_t smem) {
+  cudaFuncSetAttribute(k_batch_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+
 cudaError_t batch_launch_tc(const BatchJob* jobs, const BatchIO* io, const CUtensorMap* maps, const BItem* items,
                             int n, int grid, size_t smem, int ncol, cudaStream_t st, bool pdl) {
-  cudaFuncSetAttribute(k_batch_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   return launch_k(k_batch_expand_tc, dim3(grid), dim3(128), smem, st, pdl, jobs, io, maps, items, n, ncol);
 }
 
