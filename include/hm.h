@@ -242,10 +242,11 @@ hm_status hm_matrix_phase_times(hm_matrix* A, double ms[4], int64_t launches[4])
 
 typedef struct {
   int32_t count;             /* products in the batch */
-  int32_t launches_per_run;  /* persistent kernel launches per run (at most 5) */
-  int64_t items[5];          /* work items per phase: projection, upsweep, downsweep,
-                                SIMT expansion, tensor-core expansion */
-  int32_t grid[5];           /* persistent blocks per phase */
+  int32_t launches_per_run;  /* persistent kernel launches per run (at most 6) */
+  int64_t items[6];          /* work items per phase: SIMT projection, tensor-core
+                                projection, upsweep, downsweep, SIMT expansion,
+                                tensor-core expansion */
+  int32_t grid[6];           /* persistent blocks per phase */
   int32_t graph;             /* 1 if runs replay a captured CUDA graph */
   int32_t tuned;             /* 0 defaults, 1 tuned by timing, 2 read from the cache file */
   int32_t grid_mult;         /* tuned launch shapes: persistent blocks per SM, */
@@ -259,7 +260,7 @@ typedef struct {
  * batch.  Matrices may differ in kind (HODLR/HSS), size, tree, rank, storage
  * (HM_F32, HM_BF16, HM_BF16X2; HM_F64 returns HM_EUNSUPPORTED) and r, but
  * must live on one device and outlive the batch.  Scratch for every product is
- * reserved and the work lists of the five phases are built (each product keeps
+ * reserved and the work lists of the six phases are built (each product keeps
  * exactly the blocking it has alone, so its result is bit-identical in the
  * batch and alone).  Synchronous. */
 hm_status hm_batch_create(hm_matrix* const* A, const int64_t* r, int32_t count, hm_batch** out);
@@ -274,9 +275,10 @@ hm_status hm_batch_tune(hm_batch* b, const char* cache_path);
 
 /* Runs every product of the batch: X[j] (n_j x r_j, column-major, ld = n_j,
  * type xt: HM_F32, HM_BF16 or HM_F64) and Y[j] (ld = n_j, type yt: HM_F32 or
- * HM_F64) are device pointers.  The work is one persistent launch per phase
- * (projection, tree upsweep, HSS downsweep, SIMT expansion, tensor-core
- * expansion), recorded into a CUDA graph at the first run and replayed after.
+ * HM_F64) are device pointers.  The work is one persistent launch per
+ * non-empty phase (SIMT and tensor-core projection, tree upsweep, HSS
+ * downsweep, SIMT and tensor-core expansion), recorded into a CUDA graph at
+ * the first run and replayed after.
  * Asynchronous on `stream`; runs of one batch must not overlap. */
 hm_status hm_batch_run(hm_batch* b, const void* const* X, void* const* Y, hm_dtype xt, hm_dtype yt, void* stream);
 

@@ -47,8 +47,8 @@ class hm_matrix_info_t(C.Structure):
 
 
 class hm_batch_info_t(C.Structure):
-    _fields_ = [("count", C.c_int32), ("launches_per_run", C.c_int32), ("items", C.c_int64 * 5),
-                ("grid", C.c_int32 * 5), ("graph", C.c_int32), ("tuned", C.c_int32), ("grid_mult", C.c_int32),
+    _fields_ = [("count", C.c_int32), ("launches_per_run", C.c_int32), ("items", C.c_int64 * 6),
+                ("grid", C.c_int32 * 6), ("graph", C.c_int32), ("tuned", C.c_int32), ("grid_mult", C.c_int32),
                 ("rc_cap", C.c_int32), ("rct_cap", C.c_int32), ("tile_rows", C.c_int32),
                 ("capture_error", C.c_int32)]
 

@@ -723,7 +723,9 @@ hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int
       default: return simt_phase_bf16x2(ph, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
     }
   };
-  hm_status st = phase(0, false);
+  hm_status st = HM_EUNSUPPORTED;
+  if (use_tensor_cores(A, r)) st = launch_project_tc(A, mv, ws, r, X, ldx, xt, s, false);
+  if (st == HM_EUNSUPPORTED) st = phase(0, false);
   if (st != HM_OK) return st;
   st = phase(1, true);
   if (st != HM_OK) return st;

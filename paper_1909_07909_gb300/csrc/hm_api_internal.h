@@ -74,7 +74,11 @@ struct hm_matrix {
   hmi::Prof* prof = nullptr;   // set while profiling is enabled
   CUtensorMap tmA;              // TMA descriptors of the expansion planes (BF16 / BF16X2)
   CUtensorMap tmAlo;
+  CUtensorMap tmW;              // ... and of the projection planes
+  CUtensorMap tmWlo;
   bool tm_ok = false;
+  bool tmw_ok = false;
+  int w_box = 128;              // rows of a projection TMA box (min(Kp, 128))
   hmi::MatView view() const;
 };
 
@@ -108,8 +112,11 @@ hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int
 // Tensor-core expansion (k_tc.cu).
 void make_tensor_maps(hm_matrix* A);
 bool use_tensor_cores(const hm_matrix* A, int64_t r);
-// Shape of the tensor-core expansion of A for r columns (false if none fits).
-bool tc_plan(const hm_matrix* A, int64_t r, int* nt, int* nK, int* nX, int* nst, int* tiles);
+// Shape of the tensor-core expansion (proj = false) or projection (proj =
+// true) of A for r columns (false if none fits).
+bool tc_plan(const hm_matrix* A, int64_t r, bool proj, int* nt, int* nK, int* nX, int* nst, int* tiles);
+hm_status launch_project_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                            int64_t ldx, int xt, cudaStream_t st, bool pdl);
 size_t tc_tile_smem(bool split, int NT, int nK, int nst);
 int tc_tile_ncols(bool split, int NT);
 hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,

@@ -49,13 +49,13 @@ struct hm_batch {
   hmi::BatchKnobs knobs;
   std::vector<hmi::BatchJob> jobs;
   std::vector<hmi::BItem> items[hmi::BP_COUNT];
-  size_t smem[hmi::BP_COUNT] = {0, 0, 0, 0, 0};
-  int grid[hmi::BP_COUNT] = {0, 0, 0, 0, 0};
-  int tc_ncol = 32;
+  size_t smem[hmi::BP_COUNT] = {};
+  int grid[hmi::BP_COUNT] = {};
+  int tc_ncol[hmi::BP_COUNT] = {};
   hmi::BatchJob* d_jobs = nullptr;
   hmi::BatchIO* d_io = nullptr;
   CUtensorMap* d_maps = nullptr;
-  hmi::BItem* d_items[hmi::BP_COUNT] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  hmi::BItem* d_items[hmi::BP_COUNT] = {};
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
   std::vector<hmi::BatchIO> h_io;
@@ -95,8 +95,8 @@ static hm_status build_plan(hm_batch* b) {
   for (int p = 0; p < BP_COUNT; ++p) {
     b->items[p].clear();
     b->smem[p] = 0;
+    b->tc_ncol[p] = 32;
   }
-  b->tc_ncol = 32;
   char* sbase = static_cast<char*>(b->d_scratch);
   size_t soff = 0;
   for (int j = 0; j < b->count; ++j) {
@@ -143,13 +143,26 @@ static hm_status build_plan(hm_batch* b) {
     J.RT = kn.rt;
     J.tiles = (mv.m_pad + kn.rt - 1) / kn.rt;
     J.tc = use_tensor_cores(A, r) ? 1 : 0;
-    if (J.tc && !tc_plan(A, r, &J.nt, &J.nK, &J.nX, &J.nst, &J.tc_tiles)) J.tc = 0;
+    if (J.tc && !tc_plan(A, r, false, &J.nt, &J.nK, &J.nX, &J.nst, &J.tc_tiles)) J.tc = 0;
+    // the projection runs on the tensor cores exactly when the single product's would
+    J.tcp = (use_tensor_cores(A, r) && tc_plan(A, r, true, &J.ntp, &J.nKp, &J.nXp, &J.nstp, &J.tcp_tiles)) ? 1 : 0;
+    J.w_box = A->w_box;
     J.split = (A->storage == HM_BF16X2) ? 1 : 0;
     // work items and shared memory per phase
-    const int nch_p = static_cast<int>((r + J.rc_p - 1) / J.rc_p);
-    for (int leaf = 0; leaf < mv.L; ++leaf)
-      for (int c = 0; c < nch_p; ++c) b->items[BP_PROJECT].push_back({j, leaf, c});
-    b->smem[BP_PROJECT] = std::max(b->smem[BP_PROJECT], 4 * static_cast<size_t>(J.rc_p * mv.m_pad + J.rc_p * (mv.Kp + 1)));
+    if (J.tcp) {
+      const int nch = static_cast<int>((r + J.ntp - 1) / J.ntp);
+      for (int x = 0; x < mv.L * J.tcp_tiles; ++x)
+        for (int c = 0; c < nch; ++c) b->items[BP_PROJECT_TC].push_back({j, x, c});
+      b->smem[BP_PROJECT_TC] =
+          std::max(b->smem[BP_PROJECT_TC], 2048 + tc_tile_smem(J.split, J.ntp, J.nKp, J.nstp));
+      b->tc_ncol[BP_PROJECT_TC] = std::max(b->tc_ncol[BP_PROJECT_TC], tc_tile_ncols(J.split, J.ntp));
+    } else {
+      const int nch_p = static_cast<int>((r + J.rc_p - 1) / J.rc_p);
+      for (int leaf = 0; leaf < mv.L; ++leaf)
+        for (int c = 0; c < nch_p; ++c) b->items[BP_PROJECT].push_back({j, leaf, c});
+      b->smem[BP_PROJECT] =
+          std::max(b->smem[BP_PROJECT], 4 * static_cast<size_t>(J.rc_p * mv.m_pad + J.rc_p * (mv.Kp + 1)));
+    }
     const int nch_t = static_cast<int>((r + J.rct - 1) / J.rct);
     if (mv.p > lmin) {
       for (int x = 0; x < (mv.L >> J.s0); ++x)
@@ -168,7 +181,7 @@ static hm_status build_plan(hm_batch* b) {
       for (int x = 0; x < mv.L * J.tc_tiles; ++x)
         for (int c = 0; c < nch; ++c) b->items[BP_EXPAND_TC].push_back({j, x, c});
       b->smem[BP_EXPAND_TC] = std::max(b->smem[BP_EXPAND_TC], 2048 + tc_tile_smem(J.split, J.nt, J.nK, J.nst));
-      b->tc_ncol = std::max(b->tc_ncol, tc_tile_ncols(J.split, J.nt));
+      b->tc_ncol[BP_EXPAND_TC] = std::max(b->tc_ncol[BP_EXPAND_TC], tc_tile_ncols(J.split, J.nt));
     } else {
       const int nch_e = static_cast<int>((r + J.rc_e - 1) / J.rc_e);
       for (int x = 0; x < mv.L * J.tiles; ++x)
@@ -182,13 +195,13 @@ static hm_status build_plan(hm_batch* b) {
   // persistent grids
   for (int p = 0; p < BP_COUNT; ++p) {
     const int n = static_cast<int>(b->items[p].size());
-    int per_sm = (p == BP_EXPAND_TC) ? 1 : kn.grid_mult;
-    if (p != BP_EXPAND_TC && b->smem[p] > 0) per_sm = std::max(1, std::min(per_sm, static_cast<int>((228 * 1024) / (b->smem[p] + 1024))));
+    int per_sm = batch_phase_tc(p) ? 1 : kn.grid_mult;
+    if (!batch_phase_tc(p) && b->smem[p] > 0) per_sm = std::max(1, std::min(per_sm, static_cast<int>((228 * 1024) / (b->smem[p] + 1024))));
     b->grid[p] = std::max(0, std::min(n, b->sms * per_sm));
   }
   for (int p = 0; p < BP_COUNT; ++p) {
     if (b->items[p].empty()) continue;
-    if (p == BP_EXPAND_TC) batch_set_smem_tc(b->smem[p]);
+    if (batch_phase_tc(p)) batch_set_smem_tc(p, b->smem[p]);
     else batch_set_smem(p, b->smem[p]);
   }
   // upload
@@ -205,17 +218,17 @@ static hm_status build_plan(hm_batch* b) {
   return HM_OK;
 }
 
-// The five phase launches (projection, upsweep, downsweep, SIMT and tensor-core
-// expansion), each persistent; all but the first use programmatic
-// serialization.  Empty phases are skipped.
+// The six phase launches (SIMT and tensor-core projection, upsweep, downsweep,
+// SIMT and tensor-core expansion), each persistent; all but the first use
+// programmatic serialization.  Empty phases are skipped.
 static hm_status enqueue(hm_batch* b, cudaStream_t s) {
   bool first = true;
   for (int p = 0; p < BP_COUNT; ++p) {
     const int n = static_cast<int>(b->items[p].size());
     if (n == 0) continue;
     cudaError_t e;
-    if (p == BP_EXPAND_TC)
-      e = batch_launch_tc(b->d_jobs, b->d_io, b->d_maps, b->d_items[p], n, b->grid[p], b->smem[p], b->tc_ncol, s,
+    if (batch_phase_tc(p))
+      e = batch_launch_tc(p, b->d_jobs, b->d_io, b->d_maps, b->d_items[p], n, b->grid[p], b->smem[p], b->tc_ncol[p], s,
                           !first);
     else
       e = batch_launch_simt(p, b->d_jobs, b->d_io, b->d_items[p], n, b->grid[p], b->smem[p], s, !first);
@@ -349,14 +362,16 @@ extern "C" hm_status hm_batch_create(hm_matrix* const* A, const int64_t* r, int3
   cudaError_t e = cudaMalloc(&b->d_scratch, b->scratch_bytes);
   if (e == cudaSuccess) e = cudaMemset(b->d_scratch, 0, b->scratch_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_io, sizeof(BatchIO) * count);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * 2 * count);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * BATCH_MAPS * count);
   if (e == cudaSuccess) {
-    std::vector<CUtensorMap> maps(2 * count);
+    std::vector<CUtensorMap> maps(BATCH_MAPS * count);
     for (int j = 0; j < count; ++j) {
-      maps[2 * j] = A[j]->tmA;
-      maps[2 * j + 1] = A[j]->tmAlo;
+      maps[BATCH_MAPS * j] = A[j]->tmA;
+      maps[BATCH_MAPS * j + 1] = A[j]->tmAlo;
+      maps[BATCH_MAPS * j + 2] = A[j]->tmW;
+      maps[BATCH_MAPS * j + 3] = A[j]->tmWlo;
     }
-    e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * 2 * count, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * BATCH_MAPS * count, cudaMemcpyHostToDevice);
   }
   hm_status st = (e == cudaSuccess) ? HM_OK
                                     : bfail(e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA, "batch allocation: %s",

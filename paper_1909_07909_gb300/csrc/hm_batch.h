@@ -16,6 +16,8 @@
 namespace hmi {
 
 // One product of the batch, as the kernels see it (device memory).
+// Tensor-core fields: expansion (nt .. tc_tiles) and projection (ntp ..
+// tcp_tiles, w_box rows per TMA box of the projection planes).
 struct BatchJob {
   MatView mv;
   Scratch ws;
@@ -28,6 +30,8 @@ struct BatchJob {
   int RT, tiles;       // SIMT expansion: rows per tile, tiles per leaf
   int tc;              // 1: tensor-core expansion
   int nt, split, nK, nX, nst, tc_tiles;
+  int tcp;             // 1: tensor-core projection
+  int ntp, nKp, nXp, nstp, tcp_tiles, w_box;
 };
 
 // Per-run inputs and outputs of one product.
@@ -44,15 +48,28 @@ struct BItem {
   int job, bx, by;
 };
 
-enum { BP_PROJECT = 0, BP_UP = 1, BP_DOWN = 2, BP_EXPAND = 3, BP_EXPAND_TC = 4, BP_COUNT = 5 };
+// Phases in launch order.  Tensor maps: four per product (expansion hi/lo,
+// projection hi/lo).
+enum {
+  BP_PROJECT = 0,
+  BP_PROJECT_TC = 1,
+  BP_UP = 2,
+  BP_DOWN = 3,
+  BP_EXPAND = 4,
+  BP_EXPAND_TC = 5,
+  BP_COUNT = 6
+};
+constexpr int BATCH_MAPS = 4;
+
+inline bool batch_phase_tc(int p) { return p == BP_PROJECT_TC || p == BP_EXPAND_TC; }
 
 // Shared-memory attributes are set when a plan is built, so launches can be
 // recorded into a CUDA graph.
 void batch_set_smem(int phase, size_t smem);
-void batch_set_smem_tc(size_t smem);
+void batch_set_smem_tc(int phase, size_t smem);
 cudaError_t batch_launch_simt(int phase, const BatchJob* jobs, const BatchIO* io, const BItem* items, int n,
                               int grid, size_t smem, cudaStream_t st, bool pdl);
-cudaError_t batch_launch_tc(const BatchJob* jobs, const BatchIO* io, const CUtensorMap* maps, const BItem* items,
-                            int n, int grid, size_t smem, int ncol, cudaStream_t st, bool pdl);
+cudaError_t batch_launch_tc(int phase, const BatchJob* jobs, const BatchIO* io, const CUtensorMap* maps,
+                            const BItem* items, int n, int grid, size_t smem, int ncol, cudaStream_t st, bool pdl);
 
 }  // namespace hmi

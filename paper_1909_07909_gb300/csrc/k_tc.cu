@@ -1,5 +1,6 @@
 // Host side of the tensor-core leaf expansion: TMA descriptors of the
 // generator planes, launch configuration (see k_tc.cuh for the kernel).
+#include <cstring>
 #include <mutex>
 
 #include "k_tc.cuh"
@@ -25,26 +26,40 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-static bool plane_map(CUtensorMap* map, const void* plane, int64_t n, int We) {
+// 2-D bf16 tensor map with 128-byte swizzle: `inner` contiguous elements per
+// row, `outer` rows `row_bytes` apart, boxes of box_inner x box_outer.
+static bool encode_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                      uint32_t box_inner, uint32_t box_outer) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn || !plane) return false;
-  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(We), static_cast<cuuint64_t>(n)};
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(We) * 2};
-  const cuuint32_t box[2] = {TC_KC, TC_M};
+  if (!fn || !base) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t es[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(plane), dims, strides, box, es,
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void make_tensor_maps(hm_matrix* A) {
   A->tm_ok = false;
+  A->tmw_ok = false;
   if (A->storage != HM_BF16 && A->storage != HM_BF16X2) return;
-  if (A->n < TC_M || A->We < TC_KC) return;
-  bool ok = plane_map(&A->tmA, A->d_A, A->n, A->We);
-  if (ok && A->storage == HM_BF16X2) ok = plane_map(&A->tmAlo, A->d_A_lo, A->n, A->We);
+  if (A->n < TC_M || A->We < TC_KC || A->m_pad < TC_KC) return;
+  const bool split = (A->storage == HM_BF16X2);
+  bool ok = encode_2d(&A->tmA, A->d_A, A->We, A->n, static_cast<uint64_t>(A->We) * 2, TC_KC, TC_M);
+  if (ok && split) ok = encode_2d(&A->tmAlo, A->d_A_lo, A->We, A->n, static_cast<uint64_t>(A->We) * 2, TC_KC, TC_M);
   else A->tmAlo = A->tmA;
   A->tm_ok = ok;
+  if (A->Kp >= 8) {
+    A->w_box = std::min(A->Kp, TC_M);
+    const uint64_t rows = static_cast<uint64_t>(A->L) * A->Kp;
+    bool w = encode_2d(&A->tmW, A->d_W, A->m_pad, rows, static_cast<uint64_t>(A->m_pad) * 2, TC_KC, A->w_box);
+    if (w && split) w = encode_2d(&A->tmWlo, A->d_W_lo, A->m_pad, rows, static_cast<uint64_t>(A->m_pad) * 2, TC_KC,
+                                  A->w_box);
+    else A->tmWlo = A->tmW;
+    A->tmw_ok = w && ok;
+  }
 }
 
 bool use_tensor_cores(const hm_matrix* A, int64_t r) {
@@ -62,44 +77,21 @@ static int tc_stages(bool split, int NT, int nK) {
   return 0;
 }
 
-template <bool SPLIT, int NT>
-static hm_status launch_tc_nt(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
-                              int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
-  const int nK = (mv.We + TC_KC - 1) / TC_KC;
-  const int nX = mv.m_pad / TC_KC;
-  const int nst = tc_stages(SPLIT, NT, nK);
-  if (nst == 0) return HM_EUNSUPPORTED;
-  const size_t smem = tc_smem(SPLIT, NT, nK, nst);
-  const int tiles = (mv.m_pad + TC_M - 1) / TC_M;
-  const int nchunks = static_cast<int>((r + NT - 1) / NT);
-  cudaFuncSetAttribute(k_expand_tc<SPLIT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  Scratch wk = ws;
-  wk.prof = nullptr;
-  prof_mark(ws.prof, 3, true, st);
-  const cudaError_t e = launch_k(k_expand_tc<SPLIT, NT>, dim3(mv.L * tiles, nchunks), dim3(128), smem, st, pdl,
-                                 A->tmA, A->tmAlo, mv, wk, r, X, ldx, xt, Y, ldy, yt, tiles, nK, nX, nst);
-  prof_mark(ws.prof, 3, false, st);
-  if (e != cudaSuccess) {
-    set_error("tensor-core expansion launch failed: %s", cudaGetErrorString(e));
-    return HM_ECUDA;
-  }
-  return HM_OK;
-}
-
-bool tc_plan(const hm_matrix* A, int64_t r, int* nt, int* nK, int* nX, int* nst, int* tiles) {
+bool tc_plan(const hm_matrix* A, int64_t r, bool proj, int* nt, int* nK, int* nX, int* nst, int* tiles) {
+  if (proj && !A->tmw_ok) return false;
   const bool split = (A->storage == HM_BF16X2);
   const int64_t rr = std::min<int64_t>(r, 256);
   int NT = 16;
   while (NT < rr) NT *= 2;
-  const int k = (A->We + TC_KC - 1) / TC_KC;
+  const int k = ((proj ? A->m_pad : A->We) + TC_KC - 1) / TC_KC;
   while (NT > 16 && tc_stages(split, NT, k) == 0) NT /= 2;
   const int s = tc_stages(split, NT, k);
   if (s == 0) return false;
   *nt = NT;
   *nK = k;
-  *nX = A->m_pad / TC_KC;
+  *nX = proj ? k : A->m_pad / TC_KC;
   *nst = s;
-  *tiles = (A->m_pad + TC_M - 1) / TC_M;
+  *tiles = proj ? (A->Kp + TC_M - 1) / TC_M : (A->m_pad + TC_M - 1) / TC_M;
   return true;
 }
 
@@ -110,12 +102,49 @@ int tc_tile_ncols(bool split, int NT) {
   return NT < 32 ? 32 : NT;
 }
 
-hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
-                           int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
+// Tensor map of a bf16 X block (rows inner, columns outer) with NT-column boxes,
+// when X qualifies for TMA (16-byte aligned, ldx a multiple of 8 elements).
+static bool x_map(CUtensorMap* map, const void* X, int64_t n, int64_t r, int64_t ldx, int NT) {
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0 || (ldx & 7) != 0 || n < TC_KC) return false;
+  return encode_2d(map, X, static_cast<uint64_t>(n), static_cast<uint64_t>(r), static_cast<uint64_t>(ldx) * 2, TC_KC,
+                   static_cast<uint32_t>(NT));
+}
+
+template <bool SPLIT, int NT, bool PROJ>
+static hm_status launch_leaf_nt(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                                int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
+  int nt = 0, nK = 0, nX = 0, nst = 0, tiles = 0;
+  if (!tc_plan(A, r, PROJ, &nt, &nK, &nX, &nst, &tiles)) return HM_EUNSUPPORTED;
+  const size_t smem = tc_smem(SPLIT, NT, nK, nst);
+  const int nchunks = static_cast<int>((r + NT - 1) / NT);
+  CUtensorMap tmX;
+  std::memset(&tmX, 0, sizeof(tmX));
+  const int use_tmx = (xt == HM_BF16 && x_map(&tmX, X, mv.n, r, ldx, NT)) ? 1 : 0;
+  cudaFuncSetAttribute(k_leaf_tc<SPLIT, NT, PROJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+  Scratch wk = ws;
+  wk.prof = nullptr;
+  const int phase = PROJ ? 0 : 3;
+  prof_mark(ws.prof, phase, true, st);
+  const cudaError_t e =
+      launch_k(k_leaf_tc<SPLIT, NT, PROJ>, dim3(mv.L * tiles, nchunks), dim3(128), smem, st, pdl,
+               PROJ ? A->tmW : A->tmA, PROJ ? A->tmWlo : A->tmAlo, tmX, use_tmx, PROJ ? A->w_box : TC_M, mv, wk, r, X,
+               ldx, xt, Y, ldy, yt, tiles, nK, nX, nst);
+  prof_mark(ws.prof, phase, false, st);
+  if (e != cudaSuccess) {
+    set_error("tensor-core leaf launch failed: %s", cudaGetErrorString(e));
+    return HM_ECUDA;
+  }
+  return HM_OK;
+}
+
+template <bool PROJ>
+static hm_status launch_leaf(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                             int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
   const bool split = (A->storage == HM_BF16X2);
   int NT = 16, nK0 = 0, nX0 = 0, nst0 = 0, tiles0 = 0;
-  if (!tc_plan(A, r, &NT, &nK0, &nX0, &nst0, &tiles0)) return HM_EUNSUPPORTED;
-#define HM_TC(SP, N) return launch_tc_nt<SP, N>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl)
+  if (!tc_plan(A, r, PROJ, &NT, &nK0, &nX0, &nst0, &tiles0)) return HM_EUNSUPPORTED;
+#define HM_TC(SP, N) return launch_leaf_nt<SP, N, PROJ>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl)
   if (split) {
     switch (NT) {
       case 16: HM_TC(true, 16);
@@ -133,6 +162,16 @@ hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, i
     default: HM_TC(false, 256);
   }
 #undef HM_TC
+}
+
+hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                           int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
+  return launch_leaf<false>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
+}
+
+hm_status launch_project_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                            int64_t ldx, int xt, cudaStream_t st, bool pdl) {
+  return launch_leaf<true>(A, mv, ws, r, X, ldx, xt, nullptr, 0, 0, st, pdl);
 }
 
 }  // namespace hmi

@@ -165,12 +165,13 @@ __device__ __forceinline__ V tc_in(uint16_t x) {
 // Writes the B operand for K positions [k_begin, k_end) (multiples of 8) in
 // the K-major swizzled layout: chunk c = k / 64 holds NT rows of 128 bytes,
 // row n = right-hand side column, 16-byte unit u of the row at (u ^ (n % 8)).
-// Row k of the operand is X(a0 + k) for k < m, zero up to m_pad, then Z.
+// Row k of the operand is X(a0 + k) for k < m, zero up to m_pad, then the ke
+// rows of Z, then zero.
 // Each thread loads two 8-element groups before it converts and stores them.
 template <typename T, bool SPLIT, int NT>
 __device__ __forceinline__ void stage_b_t(uint8_t* sB, uint8_t* sBlo, int k_begin, int k_end, int tid, int nthr,
                                           const MatView& mv, const Scratch& ws, int64_t r, int leaf, int64_t a0,
-                                          int m, int col0, const T* X, int64_t ldx) {
+                                          int m, int ke, int col0, const T* X, int64_t ldx) {
   using V = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
   const int ngroups = (k_end - k_begin) >> 3;
   const int items = NT * ngroups;
@@ -216,7 +217,7 @@ __device__ __forceinline__ void stage_b_t(uint8_t* sB, uint8_t* sBlo, int k_begi
           V x = V(0);
           if (ok) {
             if (k < m) x = tc_in<V>(p[j]);
-            else if (k >= mv.m_pad && k - mv.m_pad < mv.Ke)
+            else if (k >= mv.m_pad && k - mv.m_pad < ke)
               x = static_cast<V>(z_value<float>(mv, ws, r, leaf, k - mv.m_pad, col));
           }
           v[u][j] = x;
@@ -261,15 +262,15 @@ __device__ __forceinline__ void stage_b_t(uint8_t* sB, uint8_t* sBlo, int k_begi
 template <bool SPLIT, int NT>
 __device__ __forceinline__ void stage_b(uint8_t* sB, uint8_t* sBlo, int k_begin, int k_end, int tid, int nthr,
                                         const MatView& mv, const Scratch& ws, int64_t r, int leaf, int64_t a0, int m,
-                                        int col0, const void* X, int64_t ldx, int xt) {
+                                        int ke, int col0, const void* X, int64_t ldx, int xt) {
   if (xt == HM_F32)
-    stage_b_t<float, SPLIT, NT>(sB, sBlo, k_begin, k_end, tid, nthr, mv, ws, r, leaf, a0, m, col0,
+    stage_b_t<float, SPLIT, NT>(sB, sBlo, k_begin, k_end, tid, nthr, mv, ws, r, leaf, a0, m, ke, col0,
                                 static_cast<const float*>(X), ldx);
   else if (xt == HM_F64)
-    stage_b_t<double, SPLIT, NT>(sB, sBlo, k_begin, k_end, tid, nthr, mv, ws, r, leaf, a0, m, col0,
+    stage_b_t<double, SPLIT, NT>(sB, sBlo, k_begin, k_end, tid, nthr, mv, ws, r, leaf, a0, m, ke, col0,
                                  static_cast<const double*>(X), ldx);
   else
-    stage_b_t<uint16_t, SPLIT, NT>(sB, sBlo, k_begin, k_end, tid, nthr, mv, ws, r, leaf, a0, m, col0,
+    stage_b_t<uint16_t, SPLIT, NT>(sB, sBlo, k_begin, k_end, tid, nthr, mv, ws, r, leaf, a0, m, ke, col0,
                                    static_cast<const uint16_t*>(X), ldx);
 }
 
@@ -277,7 +278,7 @@ __device__ __forceinline__ void stage_b(uint8_t* sB, uint8_t* sBlo, int k_begin,
 // the A ring, the B operand (hi and, split, lo), the barriers, the TMEM slot.
 __host__ __device__ inline size_t tc_layout_bytes(bool split, int NT, int nK, int nst) {
   const size_t stage = static_cast<size_t>(TC_M) * TC_KC * 2 * (split ? 2 : 1);
-  return nst * stage + static_cast<size_t>(nK) * NT * 128 * (split ? 2 : 1) + (2 * TC_MAX_STAGES + 1) * 8 + 16;
+  return nst * stage + static_cast<size_t>(nK) * NT * 128 * (split ? 2 : 1) + (2 * TC_MAX_STAGES + 2) * 8 + 16;
 }
 
 template <bool SPLIT, int NT>
@@ -285,15 +286,23 @@ __host__ __device__ constexpr int tc_ncols() {
   return SPLIT ? ((2 * NT <= 32) ? 32 : 2 * NT) : ((NT < 32) ? 32 : NT);
 }
 
-// One 128-row tile of one leaf with columns [col0, col0 + NT): the caller owns
-// at least tc_ncols<SPLIT, NT>() columns of tensor memory at `tmem` and a
-// 1024-byte aligned shared-memory area `base` of tc_layout_bytes(...) bytes.
-// Returns with every tensor-memory read of the tile complete and the block
-// synchronised, so the caller may start another tile or free the memory.
-template <bool SPLIT, int NT>
-__device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const MatView& mv, const Scratch& ws,
-                        int64_t r, const void* X, int64_t ldx, int xt, void* Y, int64_t ldy, int yt, int leaf,
-                        int rt, int col0, int nK, int nX, int nst, uint8_t* base, uint32_t tmem) {
+// One 128-row tile with columns [col0, col0 + NT) of one leaf's contraction:
+//   expansion (PROJ = false): Y(rows) = [D_i | E_i](rows, :) [X_i; Z_i], tile rt
+//     of the leaf's rows, K = m_pad + Ke;
+//   projection (PROJ = true): P_i = Wprj_i X_i, tile rt of the leaf's Kp
+//     projection rows (box_rows of them are loaded; the rest of the 128-row A
+//     tile is never used), K = m_pad; the result goes to the tree scratch.
+// X rows come through TMA (tmX) when X is bf16, the leaf is full (m = m_pad)
+// and its first row is 8-aligned; otherwise they are converted by the threads.
+// The caller owns at least tc_ncols<SPLIT, NT>() columns of tensor memory at
+// `tmem` and a 1024-byte aligned shared-memory area `base` of
+// tc_layout_bytes(...) bytes.  Returns with every tensor-memory read of the
+// tile complete and the block synchronised.
+template <bool SPLIT, int NT, bool PROJ>
+__device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const CUtensorMap* tmX, int box_rows,
+                        const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx, int xt,
+                        void* Y, int64_t ldy, int yt, int leaf, int rt, int col0, int nK, int nX, int nst,
+                        uint8_t* base, uint32_t tmem) {
   constexpr int A_BYTES = TC_M * TC_KC * 2;
   constexpr int STAGE_BYTES = A_BYTES * (SPLIT ? 2 : 1);
   constexpr int BCH = NT * 128;
@@ -305,16 +314,33 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
   const uint32_t full0 = smem_u32(bars);
   const uint32_t empty0 = full0 + 8 * TC_MAX_STAGES;
   const uint32_t accb = full0 + 16 * TC_MAX_STAGES;
+  const uint32_t xbar = full0 + 8 * (2 * TC_MAX_STAGES + 1);
 
   const int64_t a0 = mv.off[leaf];
   const int m = static_cast<int>(mv.off[leaf + 1] - a0);
   const int t0 = rt * TC_M;
-  if (t0 >= m) return;
-  const int nrows = min(TC_M, m - t0);
-  const int64_t row0 = a0 + t0;
+  int nrows;
+  int a_row;
+  if constexpr (PROJ) {
+    if (t0 >= mv.Kp) return;
+    nrows = min(TC_M, mv.Kp - t0);
+    a_row = leaf * mv.Kp + t0;
+  } else {
+    if (t0 >= m) return;
+    nrows = min(TC_M, m - t0);
+    a_row = static_cast<int>(a0 + t0);
+  }
+  const int a_bytes = TC_KC * box_rows * 2 * (SPLIT ? 2 : 1);   // bytes one stage's TMA writes
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   int* err = ws.err;
+  // X by TMA: bf16 input, full leaf, 16-byte aligned start row; the TMA
+  // moves the chunks of 64 X rows (nXt of them), the threads stage the rest
+  const bool x_tma = (tmX != nullptr) && xt == HM_BF16 && m == mv.m_pad && (a0 & 7) == 0;
+  const int nXt = x_tma ? mv.m_pad / TC_KC : 0;
+  const int ke = PROJ ? 0 : mv.Ke;                 // Z rows of the operand
+  // bf16 X has no lo part: the A_hi x B_lo products of X chunks vanish
+  const bool x_lo_zero = (xt == HM_BF16);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
@@ -322,21 +348,29 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(accb, 1);
+    mbar_init(xbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   auto issue = [&](int c) {
     const int s = c % nst;
     const uint32_t dst = smem_u32(sA + s * STAGE_BYTES);
-    mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-    tma_load_2d(dst, tmA, c * TC_KC, static_cast<int>(row0), full0 + 8 * s);
-    if constexpr (SPLIT) tma_load_2d(dst + A_BYTES, tmAlo, c * TC_KC, static_cast<int>(row0), full0 + 8 * s);
+    mbar_expect_tx(full0 + 8 * s, a_bytes);
+    tma_load_2d(dst, tmA, c * TC_KC, a_row, full0 + 8 * s);
+    if constexpr (SPLIT) tma_load_2d(dst + A_BYTES, tmAlo, c * TC_KC, a_row, full0 + 8 * s);
   };
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmA)) : "memory");
+    if (nXt > 0) {
+      mbar_expect_tx(xbar, static_cast<uint32_t>(nXt * BCH));
+      for (int c = 0; c < nXt; ++c)
+        tma_load_2d(smem_u32(sB + c * BCH), tmX, static_cast<int>(a0) + c * TC_KC, col0, xbar);
+    }
     for (int c = 0; c < min(nst, nK); ++c) issue(c);
   }
-  stage_b<SPLIT, NT>(sB, sBlo, 0, nX * TC_KC, threadIdx.x, 128, mv, ws, r, leaf, a0, m, col0, X, ldx, xt);
+  if (nXt < nX)
+    stage_b<SPLIT, NT>(sB, sBlo, nXt * TC_KC, nX * TC_KC, threadIdx.x, 128, mv, ws, r, leaf, a0, m, ke, col0, X, ldx,
+                       xt);
   fence_proxy_async();
   __syncthreads();
 
@@ -349,6 +383,7 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
       tc_fence_after();
       const uint32_t a_addr = smem_u32(sA + s * STAGE_BYTES);
       const uint32_t b_addr = smem_u32(sB + c * BCH);
+      const bool lo_zero = x_lo_zero && c < nX;
 #pragma unroll
       for (int k = 0; k < TC_KC / 16; ++k) {
         const uint64_t ad = sw128_desc(a_addr + k * 32);
@@ -357,9 +392,13 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
         umma_bf16(tmem, ad, bd, IDESC, acc);
         if constexpr (SPLIT) {
           const uint64_t adl = sw128_desc(a_addr + A_BYTES + k * 32);
-          const uint64_t bdl = sw128_desc(smem_u32(sBlo + c * BCH) + k * 32);
-          umma_bf16(tmem + NT, ad, bdl, IDESC, acc);
-          umma_bf16(tmem + NT, adl, bd, IDESC, 1u);
+          if (!lo_zero) {
+            const uint64_t bdl = sw128_desc(smem_u32(sBlo + c * BCH) + k * 32);
+            umma_bf16(tmem + NT, ad, bdl, IDESC, acc);
+            umma_bf16(tmem + NT, adl, bd, IDESC, 1u);
+          } else {
+            umma_bf16(tmem + NT, adl, bd, IDESC, acc);
+          }
         }
       }
       umma_commit(empty0 + 8 * s);
@@ -373,17 +412,20 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
 
   if (warp == 0) {
     bool ok = true;
-    if (lane == 0) ok = mma_chunks(0, nX);
+    if (lane == 0) {
+      if (nXt > 0) ok = mbar_wait(xbar, 0, err, 14);
+      if (ok) ok = mma_chunks(0, nX);
+    }
     __syncwarp();
-    asm volatile("bar.sync 1, 128;" ::: "memory");        // Z rows staged by warps 1..3
+    if constexpr (!PROJ) asm volatile("bar.sync 1, 128;" ::: "memory");   // Z rows staged by warps 1..3
     if (lane == 0) {
       if (ok) ok = mma_chunks(nX, nK);
       umma_commit(accb);                                   // arrives when every issued MMA is done
     }
     __syncwarp();
-  } else {
+  } else if constexpr (!PROJ) {
     pdl_wait();                                            // Z is written by the tree kernels
-    stage_b<SPLIT, NT>(sB, sBlo, nX * TC_KC, nK * TC_KC, threadIdx.x - 32, 96, mv, ws, r, leaf, a0, m, col0, X,
+    stage_b<SPLIT, NT>(sB, sBlo, nX * TC_KC, nK * TC_KC, threadIdx.x - 32, 96, mv, ws, r, leaf, a0, m, ke, col0, X,
                        ldx, xt);
     fence_proxy_async();
     asm volatile("bar.arrive 1, 128;" ::: "memory");
@@ -392,7 +434,13 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
   tc_fence_after();
   const int row = warp * 32 + lane;
   const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const int node = mv.L - 1 + leaf;
+  const int ldo = (mv.kind == HM_HODLR) ? mv.Ke : mv.Kp;
+  float* pout = static_cast<float*>(mv.kind == HM_HODLR ? ws.PS : ws.xh);
   for (int cb = 0; cb < NT; cb += 16) {
+    if constexpr (PROJ) {
+      if (warp * 32 >= nrows) break;                       // whole warp outside the projection rows
+    }
     float v[16];
     tmem_ld16(lane_addr + cb, v);
     float w[16];
@@ -402,14 +450,19 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
       for (int j = 0; j < 16; ++j) {
         const int64_t col = col0 + cb + j;
         if (col < r) {
-          const int64_t idx = (row0 + row) + col * ldy;
-          if constexpr (SPLIT) {
-            const double y = static_cast<double>(v[j]) + static_cast<double>(w[j]);
-            if (yt == HM_F64) static_cast<double*>(Y)[idx] = y;
-            else static_cast<float*>(Y)[idx] = static_cast<float>(y);
+          if constexpr (PROJ) {
+            const float y = SPLIT ? v[j] + w[j] : v[j];
+            pout[(static_cast<int64_t>(node) * r + col) * ldo + t0 + row] = y;
           } else {
-            if (yt == HM_F64) static_cast<double*>(Y)[idx] = v[j];
-            else static_cast<float*>(Y)[idx] = v[j];
+            const int64_t idx = (a0 + t0 + row) + col * ldy;
+            if constexpr (SPLIT) {
+              const double y = static_cast<double>(v[j]) + static_cast<double>(w[j]);
+              if (yt == HM_F64) static_cast<double*>(Y)[idx] = y;
+              else static_cast<float*>(Y)[idx] = static_cast<float>(y);
+            } else {
+              if (yt == HM_F64) static_cast<double*>(Y)[idx] = v[j];
+              else static_cast<float*>(Y)[idx] = v[j];
+            }
           }
         }
       }
@@ -419,11 +472,12 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
   __syncthreads();
 }
 
-template <bool SPLIT, int NT>
+template <bool SPLIT, int NT, bool PROJ>
 __global__ void __launch_bounds__(128, 1)
-    k_expand_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo, MatView mv,
-                Scratch ws, int64_t r, const void* X, int64_t ldx, int xt, void* Y, int64_t ldy, int yt,
-                int tiles_per_leaf, int nK, int nX, int nst) {
+    k_leaf_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+              const __grid_constant__ CUtensorMap tmX, int use_tmx, int box_rows, MatView mv, Scratch ws, int64_t r,
+              const void* X, int64_t ldx, int xt, void* Y, int64_t ldy, int yt, int tiles_per_leaf, int nK, int nX,
+              int nst) {
   constexpr int NCOL = tc_ncols<SPLIT, NT>();
   pdl_launch_dependents();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -432,14 +486,15 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(base + tc_layout_bytes(SPLIT, NT, nK, nst) - 16);
   const int leaf = blockIdx.x / tiles_per_leaf;
   const int rt = blockIdx.x % tiles_per_leaf;
-  if (rt * TC_M >= static_cast<int>(mv.off[leaf + 1] - mv.off[leaf])) return;
+  const int lim = PROJ ? mv.Kp : static_cast<int>(mv.off[leaf + 1] - mv.off[leaf]);
+  if (rt * TC_M >= lim) return;
   if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(tslot), NCOL);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  tc_tile<SPLIT, NT>(&tmA, &tmAlo, mv, ws, r, X, ldx, xt, Y, ldy, yt, leaf, rt, blockIdx.y * NT, nK, nX, nst, base,
-                     tmem);
+  tc_tile<SPLIT, NT, PROJ>(&tmA, &tmAlo, use_tmx ? &tmX : nullptr, box_rows, mv, ws, r, X, ldx, xt, Y, ldy, yt,
+                           leaf, rt, blockIdx.y * NT, nK, nX, nst, base, tmem);
   if ((threadIdx.x >> 5) == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, NCOL);

@@ -53,7 +53,7 @@ def test_batch_bit_identical_to_single_products():
     for j, (Yb, Ys1) in enumerate(zip(Ys, singles)):
         assert torch.equal(Yb, Ys1), j
     info = B.info()
-    assert info["launches_per_run"] <= 5
+    assert info["launches_per_run"] <= 6
     hm.device_status()
     # a few against the oracle
     for j in (0, 1, 4):

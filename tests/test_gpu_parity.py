@@ -338,6 +338,43 @@ def test_tensor_core_split_f64_output_and_bf16_input():
     assert H.col_rel_err(Y, ref) <= 1e-4
 
 
+TMA_CASES = [
+    ("hss_full_leaves_m256_r64", "hss", [256 * (i + 1) for i in range(16)], 16, 64),
+    ("hodlr_full_leaves_m144_r33", "hodlr", [144 * (i + 1) for i in range(16)], 6, 33),
+    ("hss_mixed_full_ragged_r16", "hss", OT.default_leaf_ends(4600, 150), 12, 16),
+    ("hodlr_r130_chunks", "hodlr", [256 * (i + 1) for i in range(8)], 8, 130),
+]
+
+
+@pytest.mark.parametrize("storage", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("name,kind,c,k,r", TMA_CASES)
+def test_tensor_core_bf16_x_tma_matches_staged(storage, name, kind, c, k, r):
+    """bf16 X read by TMA (ld a multiple of 8, aligned) and bf16 X staged by the
+    threads (odd ld, or a base off the 16-byte grid) build the same operand, so
+    the products agree bit for bit; both stay within the bound."""
+    g = _gens(kind, c, 17, k)
+    n = int(c[-1])
+    X = H.exact_input(np.random.default_rng(r + 5).standard_normal((n, r)), "bf16")
+    A = hm.Matrix.create(hm.Tree.from_leaf_ends(c), g, storage)
+    A.set_path(2)
+    xt = torch.from_numpy(np.ascontiguousarray(X.T)).to(H.torch_dev()).to(torch.bfloat16)
+    x_tma = xt.t()                                                   # ld = n
+    pad = torch.zeros((r, n + 3), dtype=torch.bfloat16, device=xt.device)
+    pad[:, :n] = xt
+    x_odd_ld = pad.t()[:n]                                           # ld = n + 3
+    flat = torch.zeros(r * n + 1, dtype=torch.bfloat16, device=xt.device)
+    flat[1:] = xt.reshape(-1)
+    x_shift = flat[1:].view(r, n).t()                                # base 2 bytes off
+    ys = [H.to_host(A.matmat(x, out_dtype=torch.float32)) for x in (x_tma, x_odd_ld, x_shift)]
+    hm.device_status()
+    assert np.array_equal(ys[0], ys[1]), name + ": TMA and odd-ld staging differ"
+    assert np.array_equal(ys[0], ys[2]), name + ": TMA and shifted-base staging differ"
+    ref = OM.matmat(c, g, X)
+    info = A.info()
+    fac = H.bound_factor(storage, kind, info["depth"], H.acc_length(info, kind), tensor_core=True)
+    H.check_bound(ys[0], ref, OB.envelope(c, g, X), fac, name)
+
+
 @pytest.mark.parametrize("storage", ["bf16", "bf16x2"])
 def test_tensor_core_deterministic_and_streams(storage):
     c = OT.default_leaf_ends(16384, 256)
