@@ -35,6 +35,11 @@ METRIC = "HSS/HODLR matvec GB/s, % of roofline, mixed vs FP64 at stated err; p99
 N_, LEAF, RANK, RHS = 65536, 256, 32, 64
 WORKLOAD = "hss_matmat n=65536 leaf=256 rank=32 rhs=64"
 ESZ = {"f64": 8, "f32": 4, "bf16": 2, "bf16x2": 4}
+# Right-hand-side format per storage: the BF16 tensor-core path rounds X to
+# bf16 in its operand anyway, so it takes X in bf16 (same result, half the
+# bytes, TMA-loaded); split BF16 needs the float X for its lo part.
+X_DTYPE = {"f64": "f64", "f32": "f32", "bf16": "bf16", "bf16x2": "f32"}
+XSZ = {"f64": 8, "f32": 4, "bf16": 2}
 
 
 def parse():
@@ -149,17 +154,25 @@ def step_bytes(A, storage, xs=4, ys=4):
 PHASES = ["project", "tree_up", "tree_down", "expand"]
 
 
-def phase_bytes(storage, c, xs=None):
+def phase_bytes(storage, c):
     """Algorithmic bytes per launch: the expansion reads D and U, X and writes
-    Y; the projection reads V and X; the tree kernels move only k x r blocks
-    (per-level intermediates are excluded, as for the whole step)."""
+    Y; the projection reads V and X; the tree kernels read their operators
+    once (R_V, B12, B21 upward; R_U downward; held in FP64 for FP64 storage,
+    else FP32).  Per-node k x r intermediates are excluded, as for the whole
+    step."""
     s = ESZ[storage]
-    xs = xs or (8 if storage == "f64" else 4)
-    sizes = [c[0]] + [c[i] - c[i - 1] for i in range(1, len(c))]
+    xs = XSZ[X_DTYPE[storage]]
+    ys = 8 if storage == "f64" else 4
+    ts = 8 if storage == "f64" else 4
+    L = len(c)
+    sizes = [c[0]] + [c[i] - c[i - 1] for i in range(1, L)]
     d_elems = sum(m * m for m in sizes)
-    expand = (d_elems + N_ * RANK) * s + N_ * RHS * (xs + xs)
+    expand = (d_elems + N_ * RANK) * s + N_ * RHS * (xs + ys)
     project = N_ * RANK * s + N_ * RHS * xs
-    return {"project": project, "tree_up": 0, "tree_down": 0, "expand": expand}
+    internal = L - 1
+    tree_up = internal * (2 * RANK * RANK + 2 * RANK * RANK) * ts
+    tree_down = internal * 2 * RANK * RANK * ts
+    return {"project": project, "tree_up": tree_up, "tree_down": tree_down, "expand": expand}
 
 
 def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases, clock_index=None,
@@ -168,20 +181,22 @@ def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases
     events, so consecutive kernels overlap), then a profiled pass that brackets
     every kernel with CUDA events for per-kernel durations."""
     td = torch.float64 if storage == "f64" else torch.float32
+    xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
     dev = torch.device("cuda", torch.cuda.current_device())
     mats = [hm.Matrix.create(tree, g, storage) for _ in range(copies)]
     Xh = torch.from_numpy(g["_X"].T.copy())
-    Xs = [Xh.to(dev).to(td).t() for _ in range(copies)]
+    Xs = [Xh.to(dev).to(xd).t() for _ in range(copies)]
     Ys = [torch.empty((RHS, N_), dtype=td, device=dev).t() for _ in range(copies)]
     for A in mats:
         A.reserve(RHS)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     code = hm.HM_F64 if storage == "f64" else hm.HM_F32
+    xcode = {"f64": hm.HM_F64, "f32": hm.HM_F32, "bf16": hm.HM_BF16}[X_DTYPE[storage]]
 
     def run(i):
         j = i % copies
-        mats[j].matmat_raw(RHS, Xs[j].data_ptr(), N_, code, Ys[j].data_ptr(), N_, code, sptr)
+        mats[j].matmat_raw(RHS, Xs[j].data_ptr(), N_, xcode, Ys[j].data_ptr(), N_, code, sptr)
 
     for i in range(warmup):
         run(i)
@@ -219,7 +234,7 @@ def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases
         phases = {"ms": acc_ms, "launches": acc_n, "steps": ps}
     es = 8 if storage == "f64" else 4
     res = {"ms_total": ms_total, "ms_per_step": ms_total / steps,
-           "bytes_per_step": step_bytes(mats[0], storage, es, es),
+           "bytes_per_step": step_bytes(mats[0], storage, XSZ[X_DTYPE[storage]], es),
            "phases": phases, "clocks": sampler.summary() if sampler else None,
            "generator_bytes": mats[0].generator_bytes()}
     res["gbs"] = res["bytes_per_step"] / (res["ms_per_step"] * 1e-3) / 1e9
@@ -235,21 +250,24 @@ def e2e_host(hm, torch, tree, g, storage, steps):
     A.reserve(RHS)
     f64 = storage == "f64"
     td = torch.float64 if f64 else torch.float32
-    Xp = torch.from_numpy(g["_X"].T.copy()).to(td).pin_memory()
+    xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
+    Xp = torch.from_numpy(g["_X"].T.copy()).to(xd).pin_memory()
     Yp = torch.empty((RHS, N_), dtype=td).pin_memory()
     code = hm.HM_F64 if f64 else hm.HM_F32
+    xcode = {"f64": hm.HM_F64, "f32": hm.HM_F32, "bf16": hm.HM_BF16}[X_DTYPE[storage]]
     stream = torch.cuda.current_stream().cuda_stream
     for _ in range(3):
-        A.matmat_raw(RHS, Xp.data_ptr(), N_, code, Yp.data_ptr(), N_, code, stream)
+        A.matmat_raw(RHS, Xp.data_ptr(), N_, xcode, Yp.data_ptr(), N_, code, stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        A.matmat_raw(RHS, Xp.data_ptr(), N_, code, Yp.data_ptr(), N_, code, stream)
+        A.matmat_raw(RHS, Xp.data_ptr(), N_, xcode, Yp.data_ptr(), N_, code, stream)
     dt = (time.perf_counter() - t0) / steps
     es = 8 if f64 else 4
-    b = A.generator_bytes() + N_ * RHS * 2 * es
+    xs = XSZ[X_DTYPE[storage]]
+    b = A.generator_bytes() + N_ * RHS * (xs + es)
     del np
-    return {"value": b / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": N_ * RHS * es,
+    return {"value": b / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": N_ * RHS * xs,
             "d2h_bytes_per_step": N_ * RHS * es, "ms_per_step": dt * 1e3}
 
 
@@ -581,7 +599,7 @@ def main():
                                                               "bf16x2": "bf16x2"}[prec],
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": N_, "leaf": LEAF, "rank": RANK, "rhs": RHS, "storage": prec,
-                      "x_dtype": "f64" if prec == "f64" else "f32", "y_dtype": "f64" if prec == "f64" else "f32",
+                      "x_dtype": X_DTYPE[prec], "y_dtype": "f64" if prec == "f64" else "f32",
                       "l2": "inputs larger than L2: %d rotating resident copies of %.1f MB" %
                             (copies, head["bytes_per_step"] / 1e6),
                       "generators": "leaf U,V orthonormal; R,B iid N(0,1/32) (variance); D=N(0,1)+8I; X=N(0,1)",

@@ -222,6 +222,14 @@ hm_status hm_device_status(void* stream);
  * BF16X2), 1 = SIMT only, 2 = tensor cores whenever supported. */
 hm_status hm_matrix_set_path(hm_matrix* A, int32_t path);
 
+/* Kernels for the tree phases of later products on this matrix (Sec. 4.1:
+ * the HSS upsweep, couplings and downsweep, or the HODLR per-level sums):
+ * 0 = automatic, 1 = one launch per phase with per-level handoffs through
+ * global memory, 2 = one launch of thread-block clusters that keeps the
+ * levels in shared memory, when the shape fits (else as 1).  Both sum in the
+ * same order, so the results are identical; 0 picks 2 when it fits. */
+hm_status hm_matrix_set_tree(hm_matrix* A, int32_t mode);
+
 /* Per-kernel timing of later products on this matrix: with enable = 1 every
  * kernel launch of a product is bracketed by CUDA events recorded on the
  * product's stream; enable = 0 stops recording.  Not for use under CUDA-graph

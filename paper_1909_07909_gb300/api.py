@@ -163,6 +163,10 @@ class Matrix:
     def set_path(self, path):
         check(lib.hm_matrix_set_path(self._h, int(path)), "hm_matrix_set_path")
 
+    def set_tree(self, mode):
+        """Tree-phase kernels: 0 automatic, 1 per-level launches, 2 one cluster launch (when it fits)."""
+        check(lib.hm_matrix_set_tree(self._h, int(mode)), "hm_matrix_set_tree")
+
     def profile(self, enable=True):
         """Bracket every kernel launch of later products with CUDA events."""
         check(lib.hm_matrix_profile(self._h, 1 if enable else 0), "hm_matrix_profile")

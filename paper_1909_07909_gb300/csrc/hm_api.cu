@@ -583,12 +583,22 @@ extern "C" hm_status hm_matrix_set_path(hm_matrix* A, int32_t path) {
   return HM_OK;
 }
 
+extern "C" hm_status hm_matrix_set_tree(hm_matrix* A, int32_t mode) {
+  if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
+  if (mode < 0 || mode > 2) return fail(HM_EINVAL, "tree mode must be 0, 1 or 2");
+  A->tree_mode = mode;
+  return HM_OK;
+}
+
 namespace hmi {
 
 size_t scratch_elems(const MatView& mv, int64_t r) {
   const size_t nodes = static_cast<size_t>(2 * mv.L - 1);
   if (mv.kind == HM_HODLR) return nodes * r * mv.Ke;
-  return nodes * r * (mv.Kp + 2 * static_cast<size_t>(mv.Ke));
+  // x-hat, y (couplings), y-hat, then the cluster tree kernel's couplings
+  // (one Ke x RC block per node and column chunk, r rounded up to 8)
+  const size_t r8 = static_cast<size_t>((r + 7) / 8) * 8;
+  return nodes * r * (mv.Kp + 2 * static_cast<size_t>(mv.Ke)) + nodes * r8 * mv.Ke;
 }
 
 size_t counter_count(const MatView& mv, int64_t r) {
@@ -727,9 +737,12 @@ hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int
   if (use_tensor_cores(A, r)) st = launch_project_tc(A, mv, ws, r, X, ldx, xt, s, false);
   if (st == HM_EUNSUPPORTED) st = phase(0, false);
   if (st != HM_OK) return st;
-  st = phase(1, true);
-  if (st != HM_OK) return st;
-  st = phase(2, true);
+  st = launch_tree_cluster(A, mv, ws, r, s, true);
+  if (st == HM_EUNSUPPORTED) {
+    st = phase(1, true);
+    if (st != HM_OK) return st;
+    st = phase(2, true);
+  }
   if (st != HM_OK) return st;
   if (use_tensor_cores(A, r)) {
     st = launch_expand_tc(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, true);

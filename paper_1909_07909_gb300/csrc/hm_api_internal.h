@@ -71,6 +71,10 @@ struct hm_matrix {
   size_t io_cap = 0;
   int* err = nullptr;
   int path = 0;
+  int tree_mode = 0;            // 0 automatic, 1 level kernels, 2 cluster kernel when it fits
+  int64_t tree_ok_r = -1;       // r for which the cluster kernel's residency was checked
+  bool tree_ok = false;
+  int tree_rc = 0;              // columns per cluster chosen for tree_ok_r
   hmi::Prof* prof = nullptr;   // set while profiling is enabled
   CUtensorMap tmA;              // TMA descriptors of the expansion planes (BF16 / BF16X2)
   CUtensorMap tmAlo;
@@ -115,6 +119,12 @@ bool use_tensor_cores(const hm_matrix* A, int64_t r);
 // Shape of the tensor-core expansion (proj = false) or projection (proj =
 // true) of A for r columns (false if none fits).
 bool tc_plan(const hm_matrix* A, int64_t r, bool proj, int* nt, int* nK, int* nX, int* nst, int* tiles);
+// Tree phases of one product (HSS upsweep, couplings and downsweep; HODLR
+// sums) in one cluster launch; HM_EUNSUPPORTED when the shape does not fit
+// (the level kernels then run).
+hm_status launch_tree_cluster(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
+                              bool pdl);
+bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r);
 hm_status launch_project_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                             int64_t ldx, int xt, cudaStream_t st, bool pdl);
 size_t tc_tile_smem(bool split, int NT, int nK, int nst);

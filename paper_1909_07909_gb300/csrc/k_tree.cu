@@ -1,0 +1,807 @@
+// The whole tree part of one product in one launch of thread-block clusters
+// (Sec. 4.1, Fig. 4.1): for HSS the upsweep x-hat_q = R_V^T [x-hat_a; x-hat_b]
+// with the couplings y_a = B12 x-hat_b, y_b = B21 x-hat_a (Eq. 2.2), then the
+// downsweep y-hat_c = R_U(c) y-hat_q + y_c; for HODLR the per-level sums of
+// the leaves' projections.
+//
+// One cluster of CL = 2^s CTAs per chunk of RC right-hand-side columns.  CTA j
+// owns the subtree below node j of level s: it runs those levels of both
+// sweeps in its own shared memory with block barriers only.  The s levels
+// above are shared out among the CTAs (node t of level l belongs to CTA
+// t << (s - l)); operands owned by another CTA are read through distributed
+// shared memory after a cluster barrier.  So a product pays one cluster
+// barrier per top level instead of one global-memory handoff (fence, atomic,
+// L2 round trip) per level.
+//
+// HSS operators stream through a ring of NS shared-memory slots filled by
+// cp.async.bulk copies in the order the CTA uses them (the first NS before
+// griddepcontrol.wait, overlapping the previous kernel).  The small products
+// run as warp tasks: a warp computes 32 output rows of one operator for all
+// RC columns (lane i holds row i; operator rows are conflict-free shared
+// loads, vector rows broadcasts).  A warp waits on the mbarrier of its own
+// slot; the warp that finishes the last task of a slot refills it, so the
+// ring runs ahead across level boundaries.  Every sum runs in the same order
+// as in the level kernels (fma over j from zero, then + y_c; paired FMAs
+// round each half exactly like fmaf), so both give identical bits.  Every
+// wait is bounded (2 s of %globaltimer): on expiry the kernel records an
+// error code in the library's error word and stops waiting.
+#include <type_traits>
+
+#include "hm_api_internal.h"
+#include "k_tc.cuh"
+
+namespace hmi {
+
+constexpr int TREE_THREADS = 512;
+constexpr int TREE_MAX_S = 3;          // clusters of up to 8 CTAs (portable size)
+constexpr int TREE_MAX_NS = 12;
+constexpr int TREE_MAX_ITEMS = 1040;     // node ids and consumer counts (half each)
+
+__device__ __forceinline__ uint32_t cluster_map(uint32_t saddr, int rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(saddr), "r"(rank));
+  return out;
+}
+
+__device__ __forceinline__ uint4 ld_cluster16(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Copies `units` 16-byte units from CTA `rank`'s shared memory at the same
+// offset as `src` into local `dst` (block-wide).
+__device__ __forceinline__ void pull_remote(void* dst, const void* src, int rank, int units) {
+  const uint32_t base = cluster_map(smem_u32(src), rank);
+  uint4* d = static_cast<uint4*>(dst);
+  for (int u = threadIdx.x; u < units; u += blockDim.x) d[u] = ld_cluster16(base + 16u * u);
+}
+
+// Shared-memory plan of one tree launch (offsets in bytes from a 128-byte
+// aligned base; every node vector is [j][c], K rows of RC columns).
+struct TreeLayout {
+  int s, d, K, NS;
+  uint32_t slot;                       // bytes per operator slot
+  uint32_t ctl, items, ring, A, B, TX, CH, TYC, TYF, STG, total;
+};
+
+template <typename C>
+__host__ __device__ inline uint32_t vec_bytes(int K, int RC) {
+  return static_cast<uint32_t>(K) * RC * sizeof(C);
+}
+
+// Control block: NS full barriers (8 bytes each), NS slot counters, NS
+// "item held by the slot" words, the `dead` flag and the number of requests.
+__host__ __device__ inline uint32_t ctl_bytes() { return 8 * TREE_MAX_NS + 8 * TREE_MAX_NS + 16; }
+
+template <typename C>
+__host__ __device__ inline TreeLayout tree_layout(bool hss, int p, int Kp, int Ke, int RC, int NS) {
+  TreeLayout t;
+  t.s = p < TREE_MAX_S ? p : TREE_MAX_S;
+  t.d = p - t.s;
+  t.K = Kp > Ke ? Kp : Ke;
+  t.NS = hss ? NS : 0;
+  const uint32_t up = static_cast<uint32_t>(2 * Kp * Kp + 2 * Kp * Ke) * sizeof(C);
+  const uint32_t dn = static_cast<uint32_t>(2 * Ke * Ke) * sizeof(C);
+  t.slot = hss ? (((up > dn ? up : dn) + 127u) & ~127u) : 0u;
+  const uint32_t v = vec_bytes<C>(t.K, RC);
+  const uint32_t nleaf = 1u << t.d;
+  uint32_t o = 0;
+  t.ctl = o;   o += ctl_bytes();
+  t.items = o; o += hss ? 4 * TREE_MAX_ITEMS : 0;
+  o = (o + 127u) & ~127u;
+  t.ring = o;  o += t.NS * t.slot;
+  t.A = o;     o += nleaf * v;
+  t.B = o;     o += (nleaf > 1 ? nleaf / 2 : 1) * v;
+  t.TX = o;    o += (t.s + 1) * v;               // x-hat (HODLR: T) of the owned node per top level
+  t.CH = o;    o += 2 * v;                       // stacked children of a top node
+  t.TYC = o;   o += hss ? 2 * (t.s + 1) * v : 0; // couplings of the children of owned top nodes
+  t.TYF = o;   o += hss ? (t.s + 1) * v : 0;     // y-hat of owned top nodes
+  t.STG = o;   o += 2 * v;                       // remote operands
+  t.total = o;
+  return t;
+}
+
+// The RC values of row j of a node vector.
+template <typename C, int RC>
+__device__ __forceinline__ void load_row(const C* __restrict__ v, C (&x)[RC]) {
+  if constexpr (std::is_same<C, float>::value && RC % 4 == 0) {
+#pragma unroll
+    for (int u = 0; u < RC / 4; ++u) {
+      const float4 t = reinterpret_cast<const float4*>(v)[u];
+      x[4 * u] = t.x; x[4 * u + 1] = t.y; x[4 * u + 2] = t.z; x[4 * u + 3] = t.w;
+    }
+  } else if constexpr (std::is_same<C, double>::value && RC % 2 == 0) {
+#pragma unroll
+    for (int u = 0; u < RC / 2; ++u) {
+      const double2 t = reinterpret_cast<const double2*>(v)[u];
+      x[2 * u] = t.x; x[2 * u + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < RC; ++c) x[c] = v[c];
+  }
+}
+
+// Register tile of a warp task: lane (rb, cb) owns rows rb*RT .. rb*RT+RT-1
+// and columns cb*CT .. cb*CT+CT-1 of a 32 x RC output block, so a step j
+// reads one operator row (RT contiguous values per lane) and one vector row
+// (CT per lane) with few shared-memory wavefronts.
+template <int RC>
+struct WTile {
+  static constexpr int CT = RC >= 2 ? 2 : 1;
+  static constexpr int RT = RC / CT;
+  static constexpr int NRB = 32 / RT;   // row blocks per warp
+};
+
+template <typename C, int N>
+__device__ __forceinline__ void ld_vec(const C* __restrict__ p, C (&x)[N]) {
+  if constexpr (sizeof(C) * N == 16) {
+    const uint4 t = *reinterpret_cast<const uint4*>(p);
+    memcpy(x, &t, 16);
+  } else if constexpr (sizeof(C) * N == 8) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    memcpy(x, &t, 8);
+  } else if constexpr (sizeof(C) * N == 32) {
+    const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
+    const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
+    memcpy(x, &t0, 16);
+    memcpy(reinterpret_cast<char*>(x) + 16, &t1, 16);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q) x[q] = p[q];
+  }
+}
+
+// acc[r][c] += sum over j < kj, in order, of M[j*ko + i0 + r] v[j][c0 + c]
+// (M, v in shared memory); groups of G steps load before they multiply.
+template <typename C, int RC>
+__device__ __forceinline__ void tile_acc(const C* __restrict__ M, int ko, int kj, int i0, const C* __restrict__ v,
+                                         int c0, C (&acc)[WTile<RC>::RT][WTile<RC>::CT]) {
+  constexpr int RT = WTile<RC>::RT, CT = WTile<RC>::CT;
+  constexpr int G = 8;
+  int j = 0;
+  for (; j + G <= kj; j += G) {
+    C m[G][RT];
+    C x[G][CT];
+#pragma unroll
+    for (int u = 0; u < G; ++u) ld_vec<C, RT>(M + (j + u) * ko + i0, m[u]);
+#pragma unroll
+    for (int u = 0; u < G; ++u) ld_vec<C, CT>(v + (j + u) * RC + c0, x[u]);
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      if constexpr (std::is_same<C, float>::value && CT == 2) {
+        const float2 xx = make_float2(x[u][0], x[u][1]);
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+          const float2 o = __ffma2_rn(make_float2(m[u][r], m[u][r]), xx, make_float2(acc[r][0], acc[r][1]));
+          acc[r][0] = o.x;
+          acc[r][1] = o.y;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+#pragma unroll
+          for (int c = 0; c < CT; ++c) acc[r][c] = fma(m[u][r], x[u][c], acc[r][c]);
+      }
+    }
+  }
+  for (; j < kj; ++j) {
+    C m[RT], x[CT];
+    ld_vec<C, RT>(M + j * ko + i0, m);
+    ld_vec<C, CT>(v + j * RC + c0, x);
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+      for (int c = 0; c < CT; ++c) acc[r][c] = fma(m[r], x[c], acc[r][c]);
+  }
+}
+
+// One warp task: rows row0 .. row0+31 of out = M^T v (+ add) for all RC
+// columns, where row j of v is va[j] for j < ka and vb[j - ka] after (the
+// stacked children of R_V).  M and v in shared memory; out and add ([i][c]
+// blocks) in shared or global memory; add is read before the sums, so a
+// global read overlaps them.  Rows come in multiples of 8 (ko).
+template <typename C, int RC>
+__device__ __forceinline__ void warp_task(const C* M, int ko, int kj, const C* va, int ka, const C* vb, C* out,
+                                          const C* add, int row0) {
+  constexpr int RT = WTile<RC>::RT, CT = WTile<RC>::CT, NRB = WTile<RC>::NRB;
+  const int lane = threadIdx.x & 31;
+  const int i0 = row0 + (lane % NRB) * RT;
+  const int c0 = (lane / NRB) * CT;
+  if (i0 >= ko) return;                  // ko is a multiple of 8, so rows i0 .. i0+RT-1 all exist
+  C a[RT][CT];
+  if (add) {
+#pragma unroll
+    for (int r = 0; r < RT; ++r) ld_vec<C, CT>(add + (i0 + r) * RC + c0, a[r]);
+  }
+  C acc[RT][CT];
+#pragma unroll
+  for (int r = 0; r < RT; ++r)
+#pragma unroll
+    for (int c = 0; c < CT; ++c) acc[r][c] = C(0);
+  tile_acc<C, RC>(M, ko, ka < kj ? ka : kj, i0, va, c0, acc);
+  if (kj > ka) tile_acc<C, RC>(M + ka * ko, ko, kj - ka, i0, vb, c0, acc);
+#pragma unroll
+  for (int r = 0; r < RT; ++r)
+#pragma unroll
+    for (int c = 0; c < CT; ++c) out[(i0 + r) * RC + c0 + c] = add ? acc[r][c] + a[r][c] : acc[r][c];
+}
+
+// Operator ring.  items[k]: node id | kind << 30 (0 upsweep record R_V, B12,
+// B21; 1 downsweep record R_U); cons[k]: the warp tasks that read item k.
+struct Ring {
+  uint8_t* slots;
+  uint64_t* full;
+  int* cnt;
+  int* held;                // item whose copy was last requested into the slot
+  int* dead;
+  int* issued;
+  const int* items;
+  const int* cons;          // tasks that read item k
+  int* err;
+  int NS, count;
+  uint32_t slot_bytes;
+};
+
+template <typename C>
+__device__ void ring_issue(const Ring& R, const MatView& mv, int k) {
+  if (k >= R.count) return;
+  const int it = R.items[k];
+  const int q = it & 0x3fffffff;
+  const bool down = (it >> 30) & 1;
+  const int s = k % R.NS;
+  const uint32_t dst = smem_u32(R.slots + static_cast<size_t>(s) * R.slot_bytes);
+  const uint32_t bar = smem_u32(R.full + s);
+  const int Kp = mv.Kp, Ke = mv.Ke;
+  *R.issued = k + 1;
+  // the slot's barrier phase now belongs to item k: publish that before the copy
+  *reinterpret_cast<volatile int*>(R.held + s) = k;
+  __threadfence_block();
+  if (!down) {
+    const uint32_t brv = static_cast<uint32_t>(2 * Kp * Kp) * sizeof(C);
+    const uint32_t bb = static_cast<uint32_t>(Kp * Ke) * sizeof(C);
+    mbar_expect_tx(bar, brv + 2 * bb);
+    bulk_g2s(dst, static_cast<const C*>(mv.RV) + static_cast<int64_t>(q) * 2 * Kp * Kp, brv, bar);
+    bulk_g2s(dst + brv, static_cast<const C*>(mv.B12) + static_cast<int64_t>(q) * Kp * Ke, bb, bar);
+    bulk_g2s(dst + brv + bb, static_cast<const C*>(mv.B21) + static_cast<int64_t>(q) * Kp * Ke, bb, bar);
+  } else {
+    const uint32_t bu = static_cast<uint32_t>(2 * Ke * Ke) * sizeof(C);
+    mbar_expect_tx(bar, bu);
+    bulk_g2s(dst, static_cast<const C*>(mv.RU) + static_cast<int64_t>(q) * 2 * Ke * Ke, bu, bar);
+  }
+}
+
+// Called by a whole warp before its task on item k.  The slot may still hold
+// an older item (k - NS, ...): a parity wait is only meaningful once the
+// slot's current phase is item k's, so first wait (bounded) until item k has
+// been requested into the slot, then (bounded) for its bytes.
+__device__ __forceinline__ void ring_acquire(const Ring& R, int k, int* err) {
+  if ((threadIdx.x & 31) == 0 && !*(volatile int*)R.dead) {
+    const int s = k % R.NS;
+    const volatile int* held = R.held + s;
+    bool ok = (*held == k);
+    if (!ok) {
+      const uint64_t t0 = gtimer();
+      while (!(ok = (*held == k))) {
+        if (gtimer() - t0 > TC_WAIT_NS) {
+          atomicExch(err, 22);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence_block();
+    if (!ok || !mbar_wait(smem_u32(R.full + s), (k / R.NS) & 1, err, 21)) *(volatile int*)R.dead = 1;
+  }
+  __syncwarp();
+}
+
+// Called by a whole warp after its task on item k: the last reader of the
+// slot requests item k + NS into it.
+template <typename C>
+__device__ __forceinline__ void ring_release(const Ring& R, const MatView& mv, int k) {
+  __syncwarp();
+  __threadfence_block();
+  if ((threadIdx.x & 31) == 0) {
+    const int s = k % R.NS;
+    const int old = atomicAdd(R.cnt + s, 1);
+    if (old + 1 > R.cons[k]) {                 // more readers than the item has: protocol broken
+      atomicExch(R.err, 23);
+      *(volatile int*)R.dead = 1;
+    } else if (old + 1 == R.cons[k]) {
+      R.cnt[s] = 0;
+      __threadfence_block();
+      fence_proxy_async();
+      if (!*(volatile int*)R.dead) ring_issue<C>(R, mv, k + R.NS);
+    }
+  }
+}
+
+// ld: rows per column in global memory (a multiple of 8); K: row stride of a
+// node in A.  16-byte loads, up to 8 in flight per thread, then the
+// transposing stores (consecutive threads take consecutive columns, so the
+// stores of a warp hit consecutive words).
+template <typename C, int RC>
+__device__ void load_leaves(C* A, const C* src, int64_t r, int ld, int K, int first_node, int nleaf, int col0) {
+  constexpr int E = 16 / sizeof(C);
+  const int upc = ld / E;                      // 16-byte units per column of one node
+  const int total = nleaf * RC * upc;
+  for (int base = threadIdx.x; base < total; base += blockDim.x * 8) {
+    uint4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (idx < total) {
+        const int c = idx % RC;
+        const int e = (idx / RC) % upc;
+        const int t = idx / (upc * RC);
+        const int64_t col = col0 + c;
+        if (col < r)
+          v[u] = __ldcg(reinterpret_cast<const uint4*>(src + (static_cast<int64_t>(first_node + t) * r + col) * ld) + e);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < total) {
+        const int c = idx % RC;
+        const int e = (idx / RC) % upc;
+        const int t = idx / (upc * RC);
+        const C* x = reinterpret_cast<const C*>(&v[u]);
+#pragma unroll
+        for (int q = 0; q < E; ++q) A[(t * K + e * E + q) * RC + c] = x[q];
+      }
+    }
+  }
+}
+
+// Order in which a cluster visits the n nodes (or parents) of one level:
+// rotated by the column chunk, so the clusters of a launch, which all need
+// the same operators, read different ones at a time (no hot L2 lines).
+__device__ __forceinline__ int level_perm(int t, int n) {
+  const int rot = static_cast<int>((static_cast<int64_t>(blockIdx.y) * n) / gridDim.y);
+  return (t + rot) & (n - 1);
+}
+
+template <typename C, int RC>
+__global__ void __launch_bounds__(TREE_THREADS, 1) k_tree_cluster(MatView mv, Scratch ws, int64_t r, int NS) {
+  pdl_launch_dependents();
+  extern __shared__ __align__(128) uint8_t tree_smem_raw[];
+  uint8_t* tree_smem = tree_smem_raw + ((128u - (smem_u32(tree_smem_raw) & 127u)) & 127u);
+  const bool hss = (mv.kind == HM_HSS);
+  const TreeLayout T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, NS);
+  const int s = T.s, d = T.d, p = mv.p;
+  const int Kp = mv.Kp, Ke = mv.Ke;
+  const int j = blockIdx.x;                  // rank in the cluster (grid.x = cluster size)
+  const int col0 = blockIdx.y * RC;
+  const int nleaf = 1 << d;
+  const uint32_t V = vec_bytes<C>(T.K, RC);
+  const int VS = T.K * RC;                   // elements per node vector
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  C* A = reinterpret_cast<C*>(tree_smem + T.A);
+  C* Bb = reinterpret_cast<C*>(tree_smem + T.B);
+  // couplings of the subtree's nodes: global scratch after y-hat, one Ke x RC
+  // block per (column chunk, node); written by the upsweep, read back by the
+  // downsweep of the same CTA
+  const int64_t nodes = 2 * static_cast<int64_t>(mv.L) - 1;
+  C* YCg = static_cast<C*>(ws.yf) + nodes * r * Ke + static_cast<int64_t>(blockIdx.y) * nodes * Ke * RC;
+  auto ycg = [&](int node) { return YCg + static_cast<int64_t>(node) * Ke * RC; };
+  auto vec = [&](uint32_t off, int idx) {
+    return reinterpret_cast<C*>(tree_smem + off + static_cast<size_t>(idx) * V);
+  };
+  const int nbp = (Kp + 31) / 32, nbe = (Ke + 31) / 32;   // 32-row blocks of an output
+
+  Ring R;
+  R.full = reinterpret_cast<uint64_t*>(tree_smem + T.ctl);
+  R.cnt = reinterpret_cast<int*>(tree_smem + T.ctl + 8 * TREE_MAX_NS);
+  R.held = R.cnt + TREE_MAX_NS;
+  R.dead = R.held + TREE_MAX_NS;
+  R.issued = R.dead + 1;
+  int* items = reinterpret_cast<int*>(tree_smem + T.items);
+  int* cons = items + TREE_MAX_ITEMS / 2;
+  R.items = items;
+  R.cons = cons;
+  R.err = ws.err;
+  R.slots = tree_smem + T.ring;
+  R.slot_bytes = T.slot;
+  R.NS = T.NS;
+  R.count = 0;
+
+  // ---- operator order of this CTA (HSS) and the first NS requests ----
+  if (threadIdx.x == 0) {
+    *R.dead = 0;
+    *R.issued = 0;
+    if (hss) {
+      int n = 0;
+      for (int lev = p - 1; lev >= s; --lev)                       // bottom upsweep
+        for (int t = 0; t < (1 << (lev - s)); ++t) {
+          items[n] = (1 << lev) - 1 + (j << (lev - s)) + level_perm(t, 1 << (lev - s));
+          cons[n++] = (lev > 0 ? nbp : 0) + 2 * nbe;
+        }
+      for (int lev = s - 1; lev >= 0; --lev)                       // top upsweep, owned nodes
+        if ((j & ((1 << (s - lev)) - 1)) == 0) {
+          items[n] = (1 << lev) - 1 + (j >> (s - lev));
+          cons[n++] = (lev > 0 ? nbp : 0) + 2 * nbe;
+        }
+      for (int lev = 2; lev <= s; ++lev)                           // top downsweep: the parent's record
+        if ((j & ((1 << (s - lev)) - 1)) == 0) {
+          const int node = (1 << lev) - 1 + (j >> (s - lev));
+          items[n] = (1 << 30) | ((node - 1) >> 1);
+          cons[n++] = nbe;
+        }
+      for (int lev = s + 1; lev <= p; ++lev)                       // bottom downsweep: parents
+        for (int u = 0; u < (1 << (lev - 1 - s)); ++u) {
+          items[n] = (1 << 30) | ((1 << (lev - 1)) - 1 + (j << (lev - 1 - s)) + level_perm(u, 1 << (lev - 1 - s)));
+          cons[n++] = 2 * nbe;
+        }
+      items[TREE_MAX_ITEMS / 2 - 1] = n;
+      for (int k = 0; k < T.NS; ++k) {
+        mbar_init(smem_u32(R.full + k), 1);
+        R.cnt[k] = 0;
+        R.held[k] = -1;
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  if (hss) {
+    R.count = items[TREE_MAX_ITEMS / 2 - 1];
+    if (threadIdx.x == 0)
+      for (int k = 0; k < T.NS; ++k) ring_issue<C>(R, mv, k);
+  }
+
+  pdl_wait();                               // leaf projections come from the previous kernel
+  C* data = static_cast<C*>(hss ? ws.xh : ws.PS);
+  const int ld_leaf = hss ? Kp : Ke;
+  load_leaves<C, RC>(A, data, r, ld_leaf, T.K, (1 << p) - 1 + j * nleaf, nleaf, col0);
+  __syncthreads();
+
+  int k = 0;                                // first item of the current level
+  // ---- bottom upsweep: levels p-1 .. s inside the subtree ----
+  C* cur = A;
+  C* nxt = Bb;
+  for (int lev = p - 1; lev >= s; --lev) {
+    const int nn = 1 << (lev - s);
+    const int first = (1 << lev) - 1 + (j << (lev - s));
+    if (hss) {
+      const int per = (lev > 0 ? nbp : 0) + 2 * nbe;
+      for (int w = warp; w < nn * per; w += nwarps) {
+        const int item = k + w / per;
+        const int t = level_perm(w / per, nn);
+        int b = w % per;
+        ring_acquire(R, item, ws.err);
+        const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(item % R.NS) * R.slot_bytes);
+        const C* xa = cur + static_cast<size_t>(2 * t) * VS;
+        const C* xb = xa + VS;
+        if (lev > 0 && b < nbp) {
+          warp_task<C, RC>(op, Kp, 2 * Kp, xa, Kp, xb, nxt + static_cast<size_t>(t) * VS, nullptr, 32 * b);
+        } else {
+          if (lev > 0) b -= nbp;
+          if (b < nbe)
+            warp_task<C, RC>(op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, ycg(2 * (first + t) + 1), nullptr, 32 * b);
+          else
+            warp_task<C, RC>(op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, ycg(2 * (first + t) + 2), nullptr,
+                             32 * (b - nbe));
+        }
+        ring_release<C>(R, mv, item);
+      }
+      k += nn;
+    } else {
+      // HODLR: T_q = T_a + T_b over the rows of levels 1..lev, written out for every node
+      const int rows = mv.koff[lev + 1];
+      for (int w = threadIdx.x; w < nn * rows * RC; w += blockDim.x) {
+        const int c = w % RC;
+        const int e = (w / RC) % rows;
+        const int t = w / (RC * rows);
+        const C* ch = cur + static_cast<size_t>(2 * t) * VS;
+        const C v = ch[e * RC + c] + ch[VS + e * RC + c];
+        nxt[static_cast<size_t>(t) * VS + e * RC + c] = v;
+        if (col0 + c < r) data[(static_cast<int64_t>(first + t) * r + col0 + c) * Ke + e] = v;
+      }
+    }
+    __syncthreads();
+    C* tmp = cur; cur = nxt; nxt = tmp;
+  }
+  // the subtree root (level s) -> TX[s]
+  {
+    C* tx = vec(T.TX, s);
+    for (int u = threadIdx.x; u < VS; u += blockDim.x) tx[u] = cur[u];
+  }
+  __syncthreads();
+
+  // ---- top upsweep: levels s-1 .. 0 (HODLR: .. 1), one cluster barrier each ----
+  const int lmin = hss ? 0 : 1;
+  for (int lev = s - 1; lev >= lmin; --lev) {
+    cluster_sync_all();                    // level lev+1 complete in every CTA
+    const bool own = (j & ((1 << (s - lev)) - 1)) == 0;
+    C* ch = vec(T.CH, 0);
+    if (own) {
+      const int rb = j + (1 << (s - lev - 1));                  // owner of the right child
+      const C* mine = vec(T.TX, lev + 1);
+      for (int u = threadIdx.x; u < VS; u += blockDim.x) ch[u] = mine[u];
+      pull_remote(ch + VS, vec(T.TX, lev + 1), rb, static_cast<int>(V / 16));
+    }
+    __syncthreads();
+    if (own) {
+      const int q = (1 << lev) - 1 + (j >> (s - lev));
+      if (hss) {
+        const C* xa = ch;
+        const C* xb = ch + VS;
+        const int per = (lev > 0 ? nbp : 0) + 2 * nbe;
+        for (int w = warp; w < per; w += nwarps) {
+          int b = w;
+          ring_acquire(R, k, ws.err);
+          const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(k % R.NS) * R.slot_bytes);
+          if (lev > 0 && b < nbp) {
+            warp_task<C, RC>(op, Kp, 2 * Kp, xa, Kp, xb, vec(T.TX, lev), nullptr, 32 * b);
+          } else {
+            if (lev > 0) b -= nbp;
+            if (b < nbe)
+              warp_task<C, RC>(op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, vec(T.TYC, 2 * lev), nullptr, 32 * b);
+            else
+              warp_task<C, RC>(op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, vec(T.TYC, 2 * lev + 1), nullptr,
+                               32 * (b - nbe));
+          }
+          ring_release<C>(R, mv, k);
+        }
+        ++k;
+      } else {
+        const int rows = mv.koff[lev + 1];
+        C* tx = vec(T.TX, lev);
+        for (int w = threadIdx.x; w < rows * RC; w += blockDim.x) {
+          const int c = w % RC, e = w / RC;
+          const C v = ch[e * RC + c] + ch[VS + e * RC + c];
+          tx[e * RC + c] = v;
+          if (col0 + c < r) data[(static_cast<int64_t>(q) * r + col0 + c) * Ke + e] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (hss) {
+    // ---- top downsweep: levels 1 .. s ----
+    for (int lev = 1; lev <= s; ++lev) {
+      cluster_sync_all();                  // level lev-1 (and the couplings) complete
+      const bool own = (j & ((1 << (s - lev)) - 1)) == 0;
+      C* syc = vec(T.STG, 0);
+      C* syp = vec(T.STG, 1);
+      const int node = (1 << lev) - 1 + (j >> (s - lev));
+      const int h = (node & 1) ? 0 : 1;                           // 0: left child
+      if (own) {
+        const int pj = (j >> (s - lev + 1)) << (s - lev + 1);     // owner of the parent
+        pull_remote(syc, vec(T.TYC, 2 * (lev - 1) + h), pj, static_cast<int>(V / 16));
+        if (lev >= 2) pull_remote(syp, vec(T.TYF, lev - 1), pj, static_cast<int>(V / 16));
+      }
+      __syncthreads();
+      if (own) {
+        C* yf = vec(T.TYF, lev);
+        if (lev == 1) {
+          for (int u = threadIdx.x; u < VS; u += blockDim.x) yf[u] = syc[u];
+        } else {
+          for (int w = warp; w < nbe; w += nwarps) {
+            ring_acquire(R, k, ws.err);
+            const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(k % R.NS) * R.slot_bytes);
+            warp_task<C, RC>(op + h * Ke * Ke, Ke, Ke, syp, Ke, syp, yf, syc, 32 * w);
+            ring_release<C>(R, mv, k);
+          }
+          ++k;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- bottom downsweep: levels s+1 .. p ----
+    const C* ypar = vec(T.TYF, s);
+    for (int lev = s + 1; lev <= p; ++lev) {
+      const int nc = 1 << (lev - s);                              // children at lev
+      C* out = ((p - lev) % 2 == 0) ? A : Bb;
+      const int firstc = (1 << lev) - 1 + (j << (lev - s));
+      for (int w = warp; w < nc * nbe; w += nwarps) {
+        const int b = w % nbe;
+        const int uu = (w / nbe) >> 1, hh = (w / nbe) & 1;
+        const int item = k + uu;
+        const int u = level_perm(uu, nc / 2);
+        const int t = 2 * u + hh;
+        ring_acquire(R, item, ws.err);
+        const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(item % R.NS) * R.slot_bytes);
+        const C* yp = ypar + static_cast<size_t>(u) * VS;
+        warp_task<C, RC>(op + hh * Ke * Ke, Ke, Ke, yp, Ke, yp, out + static_cast<size_t>(t) * VS, ycg(firstc + t),
+                         32 * b);
+        ring_release<C>(R, mv, item);
+      }
+      k += nc / 2;
+      __syncthreads();
+      if (lev == p) {
+        C* yg = static_cast<C*>(ws.yf);
+        const int first = (1 << lev) - 1 + (j << (lev - s));
+        const int total = nc * Ke * RC;
+        for (int w = threadIdx.x; w < total; w += blockDim.x) {
+          const int i = w % Ke;
+          const int c = (w / Ke) % RC;
+          const int t = w / (Ke * RC);
+          if (col0 + c < r)
+            yg[(static_cast<int64_t>(first + t) * r + col0 + c) * Ke + i] = out[static_cast<size_t>(t) * VS + i * RC + c];
+        }
+      }
+      ypar = out;
+    }
+    if (d == 0) {
+      // the subtree is one leaf: its y-hat is the top result
+      C* yg = static_cast<C*>(ws.yf);
+      const C* yf = vec(T.TYF, s);
+      const int node = (1 << p) - 1 + j;
+      for (int w = threadIdx.x; w < Ke * RC; w += blockDim.x) {
+        const int i = w % Ke, c = w / Ke;
+        if (col0 + c < r) yg[(static_cast<int64_t>(node) * r + col0 + c) * Ke + i] = yf[i * RC + c];
+      }
+    }
+  }
+  // no CTA leaves while another may still read its shared memory
+  cluster_sync_all();
+  if (hss && threadIdx.x == 0 && *(volatile int*)R.dead) {
+    // drain: bounded waits for the copies still in flight into the ring
+    const int hi = *R.issued;
+    for (int u = hi > T.NS ? hi - T.NS : 0; u < hi; ++u)
+      mbar_wait(smem_u32(R.full + (u % R.NS)), (u / R.NS) & 1, nullptr, 0);
+  }
+}
+
+// ---- host side ----
+
+// The layout with the deepest operator ring (up to TREE_MAX_NS slots, at
+// least 2) that fits next to the kernel's static data.
+template <typename C>
+static bool tree_fit(const MatView& mv, int RC, TreeLayout* out) {
+  const bool hss = (mv.kind == HM_HSS);
+  const uint32_t limit = 227 * 1024 - 512;
+  int NS = hss ? TREE_MAX_NS : 0;
+  TreeLayout T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, NS);
+  while (hss && NS > 2 && T.total + 128 > limit) {
+    --NS;
+    T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, NS);
+  }
+  if (T.total + 128 > limit) return false;
+  if (hss && (2 * (1 << T.d) + 2 * T.s) > TREE_MAX_ITEMS / 2 - 1) return false;
+  *out = T;
+  return true;
+}
+
+template <typename C, int RC>
+static cudaLaunchConfig_t tree_cfg(const TreeLayout& T, int64_t r, cudaStream_t st, cudaLaunchAttribute* attrs,
+                                   bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1 << T.s, static_cast<unsigned>((r + RC - 1) / RC));
+  cfg.blockDim = dim3(TREE_THREADS);
+  cfg.dynamicSmemBytes = T.total + 128;
+  cfg.stream = st;
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = 1 << T.s;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attrs[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = pdl ? 2 : 1;
+  return cfg;
+}
+
+// Clusters of this shape that can be resident at once (0 if none).
+template <typename C, int RC>
+static int tree_active(const MatView& mv, int64_t r) {
+  TreeLayout T;
+  if (!tree_fit<C>(mv, RC, &T)) return 0;
+  cudaFuncSetAttribute(k_tree_cluster<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(T.total + 128));
+  cudaLaunchAttribute attrs[2];
+  cudaLaunchConfig_t cfg = tree_cfg<C, RC>(T, r, nullptr, attrs, false);
+  int nact = 0;
+  if (cudaOccupancyMaxActiveClusters(&nact, k_tree_cluster<C, RC>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nact;
+}
+
+template <typename C, int RC>
+static hm_status launch_tree_cl(const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st, bool pdl) {
+  TreeLayout T;
+  if (!tree_fit<C>(mv, RC, &T)) return HM_EUNSUPPORTED;
+  cudaFuncSetAttribute(k_tree_cluster<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(T.total + 128));
+  cudaLaunchAttribute attrs[2];
+  cudaLaunchConfig_t cfg = tree_cfg<C, RC>(T, r, st, attrs, pdl);
+  Scratch wk = ws;
+  wk.prof = nullptr;
+  prof_mark(ws.prof, 1, true, st);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tree_cluster<C, RC>, mv, wk, r, T.NS);
+  if (e != cudaSuccess && pdl) {
+    // launch without the early start instead
+    cudaGetLastError();
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_tree_cluster<C, RC>, mv, wk, r, T.NS);
+  }
+  prof_mark(ws.prof, 1, false, st);
+  if (e != cudaSuccess) {
+    set_error("tree cluster launch failed: %s", cudaGetErrorString(e));
+    return HM_ECUDA;
+  }
+  return HM_OK;
+}
+
+template <typename C>
+static int tree_active_rc(const MatView& mv, int64_t r, int rc) {
+  switch (rc) {
+    case 1: return tree_active<C, 1>(mv, r);
+    case 2: return tree_active<C, 2>(mv, r);
+    case 4: return tree_active<C, 4>(mv, r);
+    default: return tree_active<C, 8>(mv, r);
+  }
+}
+
+// Columns per cluster: the fewest for which every cluster of the launch can
+// be resident at once; else the shape with the most resident clusters.
+template <typename C>
+static int tree_pick_rc(const MatView& mv, int64_t r) {
+  int best = 0, best_waves = 1 << 30;
+  for (int rc = 1; rc <= 8; rc *= 2) {
+    const int nact = tree_active_rc<C>(mv, r, rc);
+    if (nact <= 0) continue;
+    const int64_t ncl = (r + rc - 1) / rc;
+    const int waves = static_cast<int>((ncl + nact - 1) / nact);
+    if (waves < best_waves) {
+      best = rc;
+      best_waves = waves;
+    }
+    if (waves == 1) break;
+  }
+  return best;
+}
+
+template <typename C>
+static hm_status tree_launch_rc(const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st, bool pdl,
+                                int rc) {
+  switch (rc) {
+    case 1: return launch_tree_cl<C, 1>(mv, ws, r, st, pdl);
+    case 2: return launch_tree_cl<C, 2>(mv, ws, r, st, pdl);
+    case 4: return launch_tree_cl<C, 4>(mv, ws, r, st, pdl);
+    case 8: return launch_tree_cl<C, 8>(mv, ws, r, st, pdl);
+    default: return HM_EUNSUPPORTED;
+  }
+}
+
+bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r) {
+  const bool hss = (mv.kind == HM_HSS);
+  if (A->tree_mode == 1) return false;
+  if (mv.p < (hss ? 1 : 2) || mv.p > 10) return false;   // no tree work, or a subtree too deep
+  if (A->tree_ok_r != r) {
+    A->tree_rc = (mv.storage == HM_F64) ? tree_pick_rc<double>(mv, r) : tree_pick_rc<float>(mv, r);
+    A->tree_ok_r = r;
+    A->tree_ok = A->tree_rc > 0;
+  }
+  return A->tree_ok;
+}
+
+hm_status launch_tree_cluster(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
+                              bool pdl) {
+  if (!tree_cluster_usable(A, mv, r)) return HM_EUNSUPPORTED;
+  return (mv.storage == HM_F64) ? tree_launch_rc<double>(mv, ws, r, st, pdl, A->tree_rc)
+                                : tree_launch_rc<float>(mv, ws, r, st, pdl, A->tree_rc);
+}
+
+}  // namespace hmi
