@@ -153,6 +153,10 @@ typedef struct {
   int64_t generator_elements;  /* unpadded count: HODLR n m + 2 n k p; HSS as Sec. 2.2 */
   size_t  generator_bytes;     /* algorithmic bytes of the generators in `storage` */
   size_t  device_bytes;        /* bytes the library holds on the device for A */
+  int32_t tree_cluster;        /* tree phases of the last product: CTAs per cluster of the
+                                  one-launch tree kernel, 0 = per-level kernels (or none yet) */
+  int32_t tree_columns;        /* right-hand-side columns per cluster (0 likewise) */
+  int32_t tree_ring;           /* operator ring slots per CTA (HSS; 0 likewise or HODLR) */
 } hm_matrix_info_t;
 
 hm_status hm_matrix_info(const hm_matrix* A, hm_matrix_info_t* out);

@@ -43,7 +43,8 @@ class hm_matrix_info_t(C.Structure):
     _fields_ = [("kind", C.c_int32), ("storage", C.c_int32), ("n", C.c_int64), ("depth", C.c_int32),
                 ("num_leaves", C.c_int32), ("leaf_pad", C.c_int32), ("rank_total", C.c_int32),
                 ("generator_elements", C.c_int64), ("generator_bytes", C.c_size_t),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("tree_cluster", C.c_int32), ("tree_columns", C.c_int32),
+                ("tree_ring", C.c_int32)]
 
 
 class hm_batch_info_t(C.Structure):

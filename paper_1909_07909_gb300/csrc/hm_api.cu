@@ -566,6 +566,10 @@ extern "C" hm_status hm_matrix_info(const hm_matrix* A, hm_matrix_info_t* out) {
   out->generator_elements = A->gen_elems;
   out->generator_bytes = A->gen_bytes;
   out->device_bytes = A->dev_bytes;
+  const bool cl = A->tree_ok_r >= 0 && A->tree_ok && A->tree_mode != 1 && A->tree_last_cluster;
+  out->tree_cluster = cl ? (1 << A->tree_s) : 0;
+  out->tree_columns = cl ? A->tree_rc : 0;
+  out->tree_ring = cl ? A->tree_ns : 0;
   return HM_OK;
 }
 
@@ -738,6 +742,7 @@ hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int
   if (st == HM_EUNSUPPORTED) st = phase(0, false);
   if (st != HM_OK) return st;
   st = launch_tree_cluster(A, mv, ws, r, s, true);
+  A->tree_last_cluster = (st == HM_OK);
   if (st == HM_EUNSUPPORTED) {
     st = phase(1, true);
     if (st != HM_OK) return st;

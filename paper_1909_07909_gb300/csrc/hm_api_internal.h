@@ -74,7 +74,10 @@ struct hm_matrix {
   int tree_mode = 0;            // 0 automatic, 1 level kernels, 2 cluster kernel when it fits
   int64_t tree_ok_r = -1;       // r for which the cluster kernel's residency was checked
   bool tree_ok = false;
-  int tree_rc = 0;              // columns per cluster chosen for tree_ok_r
+  int tree_rc = 0;              // launch shape chosen for tree_ok_r: columns per cluster,
+  int tree_s = 0;               //   levels shared by the cluster (2^s CTAs),
+  int tree_ns = 0;              //   operator ring slots
+  bool tree_last_cluster = false;  // the last product ran the cluster tree kernel
   hmi::Prof* prof = nullptr;   // set while profiling is enabled
   CUtensorMap tmA;              // TMA descriptors of the expansion planes (BF16 / BF16X2)
   CUtensorMap tmAlo;

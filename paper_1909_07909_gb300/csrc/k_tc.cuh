@@ -162,6 +162,37 @@ __device__ __forceinline__ V tc_in(uint16_t x) {
   return static_cast<V>(__uint_as_float(static_cast<uint32_t>(x) << 16));
 }
 
+// Z rows e0 .. e0+7 of column `col` when they are contiguous float in the
+// tree scratch (HSS: the leaf's y-hat; HODLR: one level's T of one sibling),
+// loaded as two 16-byte vectors; false (nothing loaded) otherwise.
+template <typename V>
+__device__ __forceinline__ bool z_run8(const MatView& mv, const Scratch& ws, int64_t r, int leaf, int e0, int64_t col,
+                                       V (&out)[8]) {
+  const float* base = nullptr;
+  if (mv.kind == HM_HSS) {
+    if (mv.p == 0) return false;
+    base = static_cast<const float*>(ws.yf) + (static_cast<int64_t>(mv.L - 1 + leaf) * r + col) * mv.Ke + e0;
+  } else {
+    for (int l = 1; l <= mv.p; ++l) {
+      const int lo = mv.koff[l], hi = mv.koff[l] + mv.kk[l];
+      if (e0 < hi) {
+        if (e0 < lo || e0 + 8 > hi) return false;   // the group leaves this level's rows
+        const int anc = (1 << l) - 1 + (leaf >> (mv.p - l));
+        const int sib = (anc & 1) ? anc + 1 : anc - 1;
+        base = static_cast<const float*>(ws.PS) + (static_cast<int64_t>(sib) * r + col) * mv.Ke + e0;
+        break;
+      }
+    }
+    if (!base) return false;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const float4 a = __ldcg(reinterpret_cast<const float4*>(base));
+  const float4 b = __ldcg(reinterpret_cast<const float4*>(base) + 1);
+  out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+  out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+  return true;
+}
+
 // Writes the B operand for K positions [k_begin, k_end) (multiples of 8) in
 // the K-major swizzled layout: chunk c = k / 64 holds NT rows of 128 bytes,
 // row n = right-hand side column, 16-byte unit u of the row at (u ^ (n % 8)).
@@ -210,6 +241,8 @@ __device__ __forceinline__ void stage_b_t(uint8_t* sB, uint8_t* sBlo, int k_begi
             v[u][2 * h + 1] = __uint_as_float(w[h] & 0xffff0000u);
           }
         }
+      } else if (ok && k0 >= mv.m_pad && k0 + 8 <= mv.m_pad + ke && z_run8<V>(mv, ws, r, leaf, k0 - mv.m_pad, col, v[u])) {
+        // eight Z rows of one column, contiguous in the tree scratch: vector loads
       } else {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {

@@ -32,8 +32,8 @@
 
 namespace hmi {
 
-constexpr int TREE_THREADS = 512;
-constexpr int TREE_MAX_S = 3;          // clusters of up to 8 CTAs (portable size)
+constexpr int TREE_THREADS = 256;
+constexpr int TREE_MAX_S = 4;          // clusters of up to 16 CTAs (16: non-portable size)
 constexpr int TREE_MAX_NS = 12;
 constexpr int TREE_MAX_ITEMS = 1040;     // node ids and consumer counts (half each)
 
@@ -87,10 +87,11 @@ __host__ __device__ inline uint32_t vec_bytes(int K, int RC) {
 // "item held by the slot" words, the `dead` flag and the number of requests.
 __host__ __device__ inline uint32_t ctl_bytes() { return 8 * TREE_MAX_NS + 8 * TREE_MAX_NS + 16; }
 
+// s: levels shared by the cluster (2^s CTAs), at most p.
 template <typename C>
-__host__ __device__ inline TreeLayout tree_layout(bool hss, int p, int Kp, int Ke, int RC, int NS) {
+__host__ __device__ inline TreeLayout tree_layout(bool hss, int p, int Kp, int Ke, int RC, int NS, int s) {
   TreeLayout t;
-  t.s = p < TREE_MAX_S ? p : TREE_MAX_S;
+  t.s = p < s ? p : s;
   t.d = p - t.s;
   t.K = Kp > Ke ? Kp : Ke;
   t.NS = hss ? NS : 0;
@@ -213,32 +214,54 @@ __device__ __forceinline__ void tile_acc(const C* __restrict__ M, int ko, int kj
 // One warp task: rows row0 .. row0+31 of out = M^T v (+ add) for all RC
 // columns, where row j of v is va[j] for j < ka and vb[j - ka] after (the
 // stacked children of R_V).  M and v in shared memory; out and add ([i][c]
-// blocks) in shared or global memory; add is read before the sums, so a
-// global read overlaps them.  Rows come in multiples of 8 (ko).
+// blocks) in shared or global memory.  Split in two: wt_compute reads add
+// (before the sums, so a global read overlaps them) and the operands into
+// registers; wt_store writes the result, after the caller has released the
+// operator slot (so the release does not wait for these stores).  Rows come
+// in multiples of 8 (ko).
 template <typename C, int RC>
-__device__ __forceinline__ void warp_task(const C* M, int ko, int kj, const C* va, int ka, const C* vb, C* out,
-                                          const C* add, int row0) {
+struct WTResult {
+  C acc[WTile<RC>::RT][WTile<RC>::CT];
+  int i0, c0;
+  bool active;
+};
+
+template <typename C, int RC>
+__device__ __forceinline__ void wt_compute(WTResult<C, RC>& w, const C* M, int ko, int kj, const C* va, int ka,
+                                           const C* vb, const C* add, int row0) {
   constexpr int RT = WTile<RC>::RT, CT = WTile<RC>::CT, NRB = WTile<RC>::NRB;
   const int lane = threadIdx.x & 31;
-  const int i0 = row0 + (lane % NRB) * RT;
-  const int c0 = (lane / NRB) * CT;
-  if (i0 >= ko) return;                  // ko is a multiple of 8, so rows i0 .. i0+RT-1 all exist
+  w.i0 = row0 + (lane % NRB) * RT;
+  w.c0 = (lane / NRB) * CT;
+  w.active = w.i0 < ko;                  // ko is a multiple of 8, so rows i0 .. i0+RT-1 all exist
+  if (!w.active) return;
   C a[RT][CT];
   if (add) {
 #pragma unroll
-    for (int r = 0; r < RT; ++r) ld_vec<C, CT>(add + (i0 + r) * RC + c0, a[r]);
+    for (int r = 0; r < RT; ++r) ld_vec<C, CT>(add + (w.i0 + r) * RC + w.c0, a[r]);
   }
-  C acc[RT][CT];
 #pragma unroll
   for (int r = 0; r < RT; ++r)
 #pragma unroll
-    for (int c = 0; c < CT; ++c) acc[r][c] = C(0);
-  tile_acc<C, RC>(M, ko, ka < kj ? ka : kj, i0, va, c0, acc);
-  if (kj > ka) tile_acc<C, RC>(M + ka * ko, ko, kj - ka, i0, vb, c0, acc);
+    for (int c = 0; c < CT; ++c) w.acc[r][c] = C(0);
+  tile_acc<C, RC>(M, ko, ka < kj ? ka : kj, w.i0, va, w.c0, w.acc);
+  if (kj > ka) tile_acc<C, RC>(M + ka * ko, ko, kj - ka, w.i0, vb, w.c0, w.acc);
+  if (add) {
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+      for (int c = 0; c < CT; ++c) w.acc[r][c] = w.acc[r][c] + a[r][c];
+  }
+}
+
+template <typename C, int RC>
+__device__ __forceinline__ void wt_store(const WTResult<C, RC>& w, C* out) {
+  constexpr int RT = WTile<RC>::RT, CT = WTile<RC>::CT;
+  if (!w.active) return;
 #pragma unroll
   for (int r = 0; r < RT; ++r)
 #pragma unroll
-    for (int c = 0; c < CT; ++c) out[(i0 + r) * RC + c0 + c] = add ? acc[r][c] + a[r][c] : acc[r][c];
+    for (int c = 0; c < CT; ++c) out[(w.i0 + r) * RC + w.c0 + c] = w.acc[r][c];
 }
 
 // Operator ring.  items[k]: node id | kind << 30 (0 upsweep record R_V, B12,
@@ -379,12 +402,12 @@ __device__ __forceinline__ int level_perm(int t, int n) {
 }
 
 template <typename C, int RC>
-__global__ void __launch_bounds__(TREE_THREADS, 1) k_tree_cluster(MatView mv, Scratch ws, int64_t r, int NS) {
+__global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Scratch ws, int64_t r, int NS, int S) {
   pdl_launch_dependents();
   extern __shared__ __align__(128) uint8_t tree_smem_raw[];
   uint8_t* tree_smem = tree_smem_raw + ((128u - (smem_u32(tree_smem_raw) & 127u)) & 127u);
   const bool hss = (mv.kind == HM_HSS);
-  const TreeLayout T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, NS);
+  const TreeLayout T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, NS, S);
   const int s = T.s, d = T.d, p = mv.p;
   const int Kp = mv.Kp, Ke = mv.Ke;
   const int j = blockIdx.x;                  // rank in the cluster (grid.x = cluster size)
@@ -489,17 +512,23 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) k_tree_cluster(MatView mv, Sc
         const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(item % R.NS) * R.slot_bytes);
         const C* xa = cur + static_cast<size_t>(2 * t) * VS;
         const C* xb = xa + VS;
+        WTResult<C, RC> res;
+        C* dst;
         if (lev > 0 && b < nbp) {
-          warp_task<C, RC>(op, Kp, 2 * Kp, xa, Kp, xb, nxt + static_cast<size_t>(t) * VS, nullptr, 32 * b);
+          wt_compute<C, RC>(res, op, Kp, 2 * Kp, xa, Kp, xb, nullptr, 32 * b);
+          dst = nxt + static_cast<size_t>(t) * VS;
         } else {
           if (lev > 0) b -= nbp;
-          if (b < nbe)
-            warp_task<C, RC>(op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, ycg(2 * (first + t) + 1), nullptr, 32 * b);
-          else
-            warp_task<C, RC>(op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, ycg(2 * (first + t) + 2), nullptr,
-                             32 * (b - nbe));
+          if (b < nbe) {
+            wt_compute<C, RC>(res, op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, nullptr, 32 * b);
+            dst = ycg(2 * (first + t) + 1);
+          } else {
+            wt_compute<C, RC>(res, op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, nullptr, 32 * (b - nbe));
+            dst = ycg(2 * (first + t) + 2);
+          }
         }
         ring_release<C>(R, mv, item);
+        wt_store<C, RC>(res, dst);
       }
       k += nn;
     } else {
@@ -548,17 +577,23 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) k_tree_cluster(MatView mv, Sc
           int b = w;
           ring_acquire(R, k, ws.err);
           const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(k % R.NS) * R.slot_bytes);
+          WTResult<C, RC> res;
+          C* dst;
           if (lev > 0 && b < nbp) {
-            warp_task<C, RC>(op, Kp, 2 * Kp, xa, Kp, xb, vec(T.TX, lev), nullptr, 32 * b);
+            wt_compute<C, RC>(res, op, Kp, 2 * Kp, xa, Kp, xb, nullptr, 32 * b);
+            dst = vec(T.TX, lev);
           } else {
             if (lev > 0) b -= nbp;
-            if (b < nbe)
-              warp_task<C, RC>(op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, vec(T.TYC, 2 * lev), nullptr, 32 * b);
-            else
-              warp_task<C, RC>(op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, vec(T.TYC, 2 * lev + 1), nullptr,
-                               32 * (b - nbe));
+            if (b < nbe) {
+              wt_compute<C, RC>(res, op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, nullptr, 32 * b);
+              dst = vec(T.TYC, 2 * lev);
+            } else {
+              wt_compute<C, RC>(res, op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, nullptr, 32 * (b - nbe));
+              dst = vec(T.TYC, 2 * lev + 1);
+            }
           }
           ring_release<C>(R, mv, k);
+          wt_store<C, RC>(res, dst);
         }
         ++k;
       } else {
@@ -598,8 +633,10 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) k_tree_cluster(MatView mv, Sc
           for (int w = warp; w < nbe; w += nwarps) {
             ring_acquire(R, k, ws.err);
             const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(k % R.NS) * R.slot_bytes);
-            warp_task<C, RC>(op + h * Ke * Ke, Ke, Ke, syp, Ke, syp, yf, syc, 32 * w);
+            WTResult<C, RC> res;
+            wt_compute<C, RC>(res, op + h * Ke * Ke, Ke, Ke, syp, Ke, syp, syc, 32 * w);
             ring_release<C>(R, mv, k);
+            wt_store<C, RC>(res, yf);
           }
           ++k;
         }
@@ -621,9 +658,10 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) k_tree_cluster(MatView mv, Sc
         ring_acquire(R, item, ws.err);
         const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(item % R.NS) * R.slot_bytes);
         const C* yp = ypar + static_cast<size_t>(u) * VS;
-        warp_task<C, RC>(op + hh * Ke * Ke, Ke, Ke, yp, Ke, yp, out + static_cast<size_t>(t) * VS, ycg(firstc + t),
-                         32 * b);
+        WTResult<C, RC> res;
+        wt_compute<C, RC>(res, op + hh * Ke * Ke, Ke, Ke, yp, Ke, yp, ycg(firstc + t), 32 * b);
         ring_release<C>(R, mv, item);
+        wt_store<C, RC>(res, out + static_cast<size_t>(t) * VS);
       }
       k += nc / 2;
       __syncthreads();
@@ -664,18 +702,17 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) k_tree_cluster(MatView mv, Sc
 
 // ---- host side ----
 
-// The layout with the deepest operator ring (up to TREE_MAX_NS slots, at
-// least 2) that fits next to the kernel's static data.
+// One launch shape: levels shared by the cluster, columns per cluster, ring
+// slots (0: HODLR).
+struct TreeShape {
+  int s, rc, ns;
+};
+
 template <typename C>
-static bool tree_fit(const MatView& mv, int RC, TreeLayout* out) {
+static bool tree_fit(const MatView& mv, int RC, int s, int ns, TreeLayout* out) {
   const bool hss = (mv.kind == HM_HSS);
-  const uint32_t limit = 227 * 1024 - 512;
-  int NS = hss ? TREE_MAX_NS : 0;
-  TreeLayout T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, NS);
-  while (hss && NS > 2 && T.total + 128 > limit) {
-    --NS;
-    T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, NS);
-  }
+  const uint32_t limit = 227 * 1024 - 512;   // 128 bytes of alignment slack, static data
+  const TreeLayout T = tree_layout<C>(hss, mv.p, mv.Kp, mv.Ke, RC, hss ? ns : 0, s);
   if (T.total + 128 > limit) return false;
   if (hss && (2 * (1 << T.d) + 2 * T.s) > TREE_MAX_ITEMS / 2 - 1) return false;
   *out = T;
@@ -701,13 +738,18 @@ static cudaLaunchConfig_t tree_cfg(const TreeLayout& T, int64_t r, cudaStream_t 
   return cfg;
 }
 
+template <typename C, int RC>
+static void tree_attrs(size_t smem) {
+  cudaFuncSetAttribute(k_tree_cluster<C, RC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_tree_cluster<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+
 // Clusters of this shape that can be resident at once (0 if none).
 template <typename C, int RC>
-static int tree_active(const MatView& mv, int64_t r) {
+static int tree_active(const MatView& mv, int64_t r, int s, int ns) {
   TreeLayout T;
-  if (!tree_fit<C>(mv, RC, &T)) return 0;
-  cudaFuncSetAttribute(k_tree_cluster<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(T.total + 128));
+  if (!tree_fit<C>(mv, RC, s, ns, &T)) return 0;
+  tree_attrs<C, RC>(T.total + 128);
   cudaLaunchAttribute attrs[2];
   cudaLaunchConfig_t cfg = tree_cfg<C, RC>(T, r, nullptr, attrs, false);
   int nact = 0;
@@ -718,23 +760,91 @@ static int tree_active(const MatView& mv, int64_t r) {
   return nact;
 }
 
+template <typename C>
+static int tree_active_rc(const MatView& mv, int64_t r, const TreeShape& sh) {
+  switch (sh.rc) {
+    case 1: return tree_active<C, 1>(mv, r, sh.s, sh.ns);
+    case 2: return tree_active<C, 2>(mv, r, sh.s, sh.ns);
+    case 4: return tree_active<C, 4>(mv, r, sh.s, sh.ns);
+    default: return tree_active<C, 8>(mv, r, sh.s, sh.ns);
+  }
+}
+
+// The deepest ring (up to TREE_MAX_NS slots, at least 2) that fits in `budget`
+// bytes of shared memory; 0 if none does.
+template <typename C>
+static int tree_ring(const MatView& mv, int RC, int s, uint32_t budget) {
+  const bool hss = (mv.kind == HM_HSS);
+  if (!hss) {
+    const TreeLayout T = tree_layout<C>(false, mv.p, mv.Kp, mv.Ke, RC, 0, s);
+    return (T.total + 128 <= budget) ? 1 : 0;
+  }
+  for (int ns = TREE_MAX_NS; ns >= 2; --ns) {
+    const TreeLayout T = tree_layout<C>(true, mv.p, mv.Kp, mv.Ke, RC, ns, s);
+    if (T.total + 128 <= budget) return ns;
+  }
+  return 0;
+}
+
+// Picks the launch shape with the fewest waves of clusters and, among those,
+// the least estimated time per CTA.
+template <typename C>
+static bool tree_pick(const MatView& mv, int64_t r, TreeShape* out) {
+  bool found = false;
+  double best = 1e300;
+  int best_waves = 1 << 30;
+  const int smax = mv.p < TREE_MAX_S ? mv.p : TREE_MAX_S;
+  for (int s = (smax >= 3 ? 3 : smax); s <= smax; ++s) {
+    for (int rc = 1; rc <= 8; rc *= 2) {
+      // a deep ring at one CTA per SM, or a shallower one that lets two share an SM
+      const uint32_t budgets[2] = {227u * 1024 - 512, 113u * 1024 - 256};
+      for (uint32_t budget : budgets) {
+        const int ns = tree_ring<C>(mv, rc, s, budget);
+        if (ns == 0) continue;
+        TreeShape sh{s, rc, mv.kind == HM_HSS ? ns : 0};
+        TreeLayout T;
+        if (!tree_fit<C>(mv, rc, s, sh.ns, &T)) continue;
+        const int nact = tree_active_rc<C>(mv, r, sh);
+        if (nact <= 0) continue;
+        const int64_t ncl = (r + rc - 1) / rc;
+        const int waves = static_cast<int>((ncl + nact - 1) / nact);
+        // estimated cycles of one CTA: the larger of its shared-memory
+        // wavefronts (6K steps per node pair, RT + CT per step) and its
+        // operator stream (2 records per subtree node, ~2300 cycles per copy,
+        // ns in flight), plus ~2000 cycles per top level
+        const int K = mv.Kp > mv.Ke ? mv.Kp : mv.Ke;
+        const double wav = static_cast<double>(1 << T.d) * 6.0 * K * (rc >= 2 ? rc / 2 + 2 : 2);
+        const double stream = (sh.ns > 0) ? 2.0 * (1 << T.d) * 2300.0 / sh.ns : 0.0;
+        const double score = ((wav > stream ? wav : stream) + 2000.0 * T.s) * waves;
+        if (waves < best_waves || (waves == best_waves && score < best)) {
+          best_waves = waves;
+          best = score;
+          *out = sh;
+          found = true;
+        }
+      }
+    }
+  }
+  return found;
+}
+
 template <typename C, int RC>
-static hm_status launch_tree_cl(const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st, bool pdl) {
+static hm_status launch_tree_cl(const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st, bool pdl,
+                                const TreeShape& sh) {
   TreeLayout T;
-  if (!tree_fit<C>(mv, RC, &T)) return HM_EUNSUPPORTED;
-  cudaFuncSetAttribute(k_tree_cluster<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(T.total + 128));
+  if (!tree_fit<C>(mv, RC, sh.s, sh.ns, &T)) return HM_EUNSUPPORTED;
+  tree_attrs<C, RC>(T.total + 128);
   cudaLaunchAttribute attrs[2];
   cudaLaunchConfig_t cfg = tree_cfg<C, RC>(T, r, st, attrs, pdl);
   Scratch wk = ws;
   wk.prof = nullptr;
   prof_mark(ws.prof, 1, true, st);
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tree_cluster<C, RC>, mv, wk, r, T.NS);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tree_cluster<C, RC>, mv, wk, r, T.NS, T.s);
   if (e != cudaSuccess && pdl) {
     // launch without the early start instead
     cudaGetLastError();
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_tree_cluster<C, RC>, mv, wk, r, T.NS);
+    e = cudaLaunchKernelEx(&cfg, k_tree_cluster<C, RC>, mv, wk, r, T.NS, T.s);
   }
   prof_mark(ws.prof, 1, false, st);
   if (e != cudaSuccess) {
@@ -745,42 +855,13 @@ static hm_status launch_tree_cl(const MatView& mv, const Scratch& ws, int64_t r,
 }
 
 template <typename C>
-static int tree_active_rc(const MatView& mv, int64_t r, int rc) {
-  switch (rc) {
-    case 1: return tree_active<C, 1>(mv, r);
-    case 2: return tree_active<C, 2>(mv, r);
-    case 4: return tree_active<C, 4>(mv, r);
-    default: return tree_active<C, 8>(mv, r);
-  }
-}
-
-// Columns per cluster: the fewest for which every cluster of the launch can
-// be resident at once; else the shape with the most resident clusters.
-template <typename C>
-static int tree_pick_rc(const MatView& mv, int64_t r) {
-  int best = 0, best_waves = 1 << 30;
-  for (int rc = 1; rc <= 8; rc *= 2) {
-    const int nact = tree_active_rc<C>(mv, r, rc);
-    if (nact <= 0) continue;
-    const int64_t ncl = (r + rc - 1) / rc;
-    const int waves = static_cast<int>((ncl + nact - 1) / nact);
-    if (waves < best_waves) {
-      best = rc;
-      best_waves = waves;
-    }
-    if (waves == 1) break;
-  }
-  return best;
-}
-
-template <typename C>
-static hm_status tree_launch_rc(const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st, bool pdl,
-                                int rc) {
-  switch (rc) {
-    case 1: return launch_tree_cl<C, 1>(mv, ws, r, st, pdl);
-    case 2: return launch_tree_cl<C, 2>(mv, ws, r, st, pdl);
-    case 4: return launch_tree_cl<C, 4>(mv, ws, r, st, pdl);
-    case 8: return launch_tree_cl<C, 8>(mv, ws, r, st, pdl);
+static hm_status tree_launch_shape(const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st, bool pdl,
+                                   const TreeShape& sh) {
+  switch (sh.rc) {
+    case 1: return launch_tree_cl<C, 1>(mv, ws, r, st, pdl, sh);
+    case 2: return launch_tree_cl<C, 2>(mv, ws, r, st, pdl, sh);
+    case 4: return launch_tree_cl<C, 4>(mv, ws, r, st, pdl, sh);
+    case 8: return launch_tree_cl<C, 8>(mv, ws, r, st, pdl, sh);
     default: return HM_EUNSUPPORTED;
   }
 }
@@ -788,11 +869,14 @@ static hm_status tree_launch_rc(const MatView& mv, const Scratch& ws, int64_t r,
 bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r) {
   const bool hss = (mv.kind == HM_HSS);
   if (A->tree_mode == 1) return false;
-  if (mv.p < (hss ? 1 : 2) || mv.p > 10) return false;   // no tree work, or a subtree too deep
+  if (mv.p < (hss ? 1 : 2) || mv.p > 11) return false;   // no tree work, or a subtree too deep
   if (A->tree_ok_r != r) {
-    A->tree_rc = (mv.storage == HM_F64) ? tree_pick_rc<double>(mv, r) : tree_pick_rc<float>(mv, r);
+    TreeShape sh{0, 0, 0};
+    A->tree_ok = (mv.storage == HM_F64) ? tree_pick<double>(mv, r, &sh) : tree_pick<float>(mv, r, &sh);
+    A->tree_s = sh.s;
+    A->tree_rc = sh.rc;
+    A->tree_ns = sh.ns;
     A->tree_ok_r = r;
-    A->tree_ok = A->tree_rc > 0;
   }
   return A->tree_ok;
 }
@@ -800,8 +884,9 @@ bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r) {
 hm_status launch_tree_cluster(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
                               bool pdl) {
   if (!tree_cluster_usable(A, mv, r)) return HM_EUNSUPPORTED;
-  return (mv.storage == HM_F64) ? tree_launch_rc<double>(mv, ws, r, st, pdl, A->tree_rc)
-                                : tree_launch_rc<float>(mv, ws, r, st, pdl, A->tree_rc);
+  const TreeShape sh{A->tree_s, A->tree_rc, A->tree_ns};
+  return (mv.storage == HM_F64) ? tree_launch_shape<double>(mv, ws, r, st, pdl, sh)
+                                : tree_launch_shape<float>(mv, ws, r, st, pdl, sh);
 }
 
 }  // namespace hmi
