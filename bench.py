@@ -411,7 +411,6 @@ def run_batched(args):
             t0 = time.perf_counter()
             B.tune(None)
             entry["tune_s"] = time.perf_counter() - t0
-            info = B.info()
             for _ in range(args.warmup):
                 B.run(Xs, Ys)
             torch.cuda.synchronize()
@@ -421,8 +420,10 @@ def run_batched(args):
             e1.record(st)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / args.steps
+            info = B.info()          # after the runs: the first run after tuning records the graph
             entry.update({"batched_ms": ms, "batched_gbs": step_bytes / (ms * 1e-3) / 1e9,
                           "launches_per_run": info["launches_per_run"], "graph": info["graph"],
+                          "capture_error": info["capture_error"],
                           "tuned": {k: info[k] for k in ("grid_mult", "rc_cap", "rct_cap", "tile_rows")}})
         loops = max(1, args.steps // 4)
         for _ in range(2):
