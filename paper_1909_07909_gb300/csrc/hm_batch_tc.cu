@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(128, 1)
       const int nst = PROJ ? J.nstp : J.nst;
 #define HM_T(SP, N)                                                                                             \
   tc_tile<SP, N, PROJ>(ma, ml, nullptr, box, J.mv, J.ws, J.r, o.X, o.ldx, o.xt, o.Y, o.ldy, o.yt, leaf, rt, col0, \
-                       nK, nX, nst, tile_base, tmem);                                                            \
+                       nK, nX, nst, tile_base, tmem, 1);                                                            \
   break
       if (J.split) {
         switch (nt) {

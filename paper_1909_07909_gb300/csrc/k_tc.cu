@@ -68,7 +68,33 @@ bool use_tensor_cores(const hm_matrix* A, int64_t r) {
   return A->path == 2 || r >= 16;
 }
 
-static size_t tc_smem(bool split, int NT, int nK, int nst) { return 1024 + tc_layout_bytes(split, NT, nK, nst); }
+static size_t tc_smem(bool split, int NT, int nK, int nst, int mt = 1) {
+  return 1024 + tc_layout_bytes(split, NT, nK, nst, mt);
+}
+
+// Tiles per CTA of a single product's expansion: two 128-row tiles of a leaf
+// share one CTA (one B operand, X read once per leaf, half the CTAs) when the
+// leaf has two, the accumulators fit in tensor memory and a 2-stage ring
+// fits; the ring is then as deep as two CTAs per SM allow when the grid
+// exceeds one CTA per SM, else as deep as fits.
+static void tc_pick_mt(bool split, int NT, int nK, int tiles128, int64_t ctas_mt2, int sms, int* mt, int* nst) {
+  *mt = 1;
+  if (tiles128 < 2 || 2 * tc_ncols_host(split, NT) > 512) return;
+  const size_t two_per_sm = 113 * 1024;
+  int best = 0;
+  for (int s = TC_MAX_STAGES; s >= 2; --s) {
+    const size_t b = tc_smem(split, NT, nK, s, 2);
+    if (b > 227 * 1024) continue;
+    if (best == 0) best = s;                       // deepest that fits at all
+    if (ctas_mt2 > sms && b <= two_per_sm) {       // deepest that lets two CTAs share an SM
+      best = s;
+      break;
+    }
+  }
+  if (best == 0) return;
+  *mt = 2;
+  *nst = best;
+}
 
 // Deepest ring (4..2 stages) whose shared memory fits; 0 if none does.
 static int tc_stages(bool split, int NT, int nK) {
@@ -97,10 +123,7 @@ bool tc_plan(const hm_matrix* A, int64_t r, bool proj, int* nt, int* nK, int* nX
 
 size_t tc_tile_smem(bool split, int NT, int nK, int nst) { return tc_layout_bytes(split, NT, nK, nst); }
 
-int tc_tile_ncols(bool split, int NT) {
-  if (split) return (2 * NT <= 32) ? 32 : 2 * NT;
-  return NT < 32 ? 32 : NT;
-}
+int tc_tile_ncols(bool split, int NT) { return tc_ncols_host(split, NT); }
 
 // Tensor map of a bf16 X block (rows inner, columns outer) with NT-column boxes,
 // when X qualifies for TMA (16-byte aligned, ldx a multiple of 8 elements).
@@ -115,8 +138,20 @@ static hm_status launch_leaf_nt(hm_matrix* A, const MatView& mv, const Scratch& 
                                 int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
   int nt = 0, nK = 0, nX = 0, nst = 0, tiles = 0;
   if (!tc_plan(A, r, PROJ, &nt, &nK, &nX, &nst, &tiles)) return HM_EUNSUPPORTED;
-  const size_t smem = tc_smem(SPLIT, NT, nK, nst);
   const int nchunks = static_cast<int>((r + NT - 1) / NT);
+  int mt = 1;
+  if (!PROJ) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nst2 = nst;
+    tc_pick_mt(SPLIT, NT, nK, tiles, static_cast<int64_t>(mv.L) * ((tiles + 1) / 2) * nchunks, sms, &mt, &nst2);
+    if (mt == 2) {
+      nst = nst2;
+      tiles = (tiles + 1) / 2;
+    }
+  }
+  const size_t smem = tc_smem(SPLIT, NT, nK, nst, mt);
   CUtensorMap tmX;
   std::memset(&tmX, 0, sizeof(tmX));
   const int use_tmx = (xt == HM_BF16 && x_map(&tmX, X, mv.n, r, ldx, NT)) ? 1 : 0;
@@ -129,7 +164,7 @@ static hm_status launch_leaf_nt(hm_matrix* A, const MatView& mv, const Scratch& 
   const cudaError_t e =
       launch_k(k_leaf_tc<SPLIT, NT, PROJ>, dim3(mv.L * tiles, nchunks), dim3(128), smem, st, pdl,
                PROJ ? A->tmW : A->tmA, PROJ ? A->tmWlo : A->tmAlo, tmX, use_tmx, PROJ ? A->w_box : TC_M, mv, wk, r, X,
-               ldx, xt, Y, ldy, yt, tiles, nK, nX, nst);
+               ldx, xt, Y, ldy, yt, tiles, nK, nX, nst, mt);
   prof_mark(ws.prof, phase, false, st);
   if (e != cudaSuccess) {
     set_error("tensor-core leaf launch failed: %s", cudaGetErrorString(e));

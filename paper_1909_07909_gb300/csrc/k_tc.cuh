@@ -307,10 +307,11 @@ __device__ __forceinline__ void stage_b(uint8_t* sB, uint8_t* sBlo, int k_begin,
                                    static_cast<const uint16_t*>(X), ldx);
 }
 
-// Shared-memory bytes of one tile (after 1024-byte alignment of the base):
-// the A ring, the B operand (hi and, split, lo), the barriers, the TMEM slot.
-__host__ __device__ inline size_t tc_layout_bytes(bool split, int NT, int nK, int nst) {
-  const size_t stage = static_cast<size_t>(TC_M) * TC_KC * 2 * (split ? 2 : 1);
+// Shared-memory bytes of one CTA's work (after 1024-byte alignment of the
+// base): the A ring (mt 128-row tiles per stage), the B operand (hi and,
+// split, lo), the barriers, the TMEM slot.
+__host__ __device__ inline size_t tc_layout_bytes(bool split, int NT, int nK, int nst, int mt = 1) {
+  const size_t stage = static_cast<size_t>(mt) * TC_M * TC_KC * 2 * (split ? 2 : 1);
   return nst * stage + static_cast<size_t>(nK) * NT * 128 * (split ? 2 : 1) + (2 * TC_MAX_STAGES + 2) * 8 + 16;
 }
 
@@ -319,7 +320,14 @@ __host__ __device__ constexpr int tc_ncols() {
   return SPLIT ? ((2 * NT <= 32) ? 32 : 2 * NT) : ((NT < 32) ? 32 : NT);
 }
 
-// One 128-row tile with columns [col0, col0 + NT) of one leaf's contraction:
+// Tensor-memory columns of one tile's accumulators (a power of two, >= 32).
+__host__ __device__ inline int tc_ncols_host(bool split, int NT) {
+  return split ? ((2 * NT <= 32) ? 32 : 2 * NT) : ((NT < 32) ? 32 : NT);
+}
+
+// mt (1 or 2) consecutive 128-row tiles with columns [col0, col0 + NT) of one
+// leaf's contraction; the tiles share the B operand and use one accumulator
+// set each (TMEM columns u * tc_ncols<SPLIT, NT>() onwards):
 //   expansion (PROJ = false): Y(rows) = [D_i | E_i](rows, :) [X_i; Z_i], tile rt
 //     of the leaf's rows, K = m_pad + Ke;
 //   projection (PROJ = true): P_i = Wprj_i X_i, tile rt of the leaf's Kp
@@ -327,17 +335,19 @@ __host__ __device__ constexpr int tc_ncols() {
 //     tile is never used), K = m_pad; the result goes to the tree scratch.
 // X rows come through TMA (tmX) when X is bf16, the leaf is full (m = m_pad)
 // and its first row is 8-aligned; otherwise they are converted by the threads.
-// The caller owns at least tc_ncols<SPLIT, NT>() columns of tensor memory at
-// `tmem` and a 1024-byte aligned shared-memory area `base` of
-// tc_layout_bytes(...) bytes.  Returns with every tensor-memory read of the
-// tile complete and the block synchronised.
+// The caller owns at least mt * tc_ncols<SPLIT, NT>() columns of tensor
+// memory at `tmem` and a 1024-byte aligned shared-memory area `base` of
+// tc_layout_bytes(..., mt) bytes.  Returns with every tensor-memory read
+// complete and the block synchronised.  Each tile's result is the same
+// whatever mt is.
 template <bool SPLIT, int NT, bool PROJ>
 __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const CUtensorMap* tmX, int box_rows,
                         const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx, int xt,
                         void* Y, int64_t ldy, int yt, int leaf, int rt, int col0, int nK, int nX, int nst,
-                        uint8_t* base, uint32_t tmem) {
+                        uint8_t* base, uint32_t tmem, int mt = 1) {
   constexpr int A_BYTES = TC_M * TC_KC * 2;
-  constexpr int STAGE_BYTES = A_BYTES * (SPLIT ? 2 : 1);
+  const int STAGE_BYTES = A_BYTES * (SPLIT ? 2 : 1) * mt;
+  constexpr int TPT = tc_ncols<SPLIT, NT>();       // TMEM columns per tile
   constexpr int BCH = NT * 128;
   constexpr uint32_t IDESC = idesc_bf16(TC_M, NT);
   uint8_t* sA = base;
@@ -351,19 +361,19 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
 
   const int64_t a0 = mv.off[leaf];
   const int m = static_cast<int>(mv.off[leaf + 1] - a0);
-  const int t0 = rt * TC_M;
-  int nrows;
+  const int t0 = rt * TC_M * mt;
+  int lim;                                           // rows of this leaf's output
   int a_row;
   if constexpr (PROJ) {
     if (t0 >= mv.Kp) return;
-    nrows = min(TC_M, mv.Kp - t0);
+    lim = mv.Kp;
     a_row = leaf * mv.Kp + t0;
   } else {
     if (t0 >= m) return;
-    nrows = min(TC_M, m - t0);
+    lim = m;
     a_row = static_cast<int>(a0 + t0);
   }
-  const int a_bytes = TC_KC * box_rows * 2 * (SPLIT ? 2 : 1);   // bytes one stage's TMA writes
+  const int a_bytes = TC_KC * box_rows * 2 * (SPLIT ? 2 : 1) * mt;   // bytes one stage's TMA writes
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   int* err = ws.err;
@@ -389,8 +399,10 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
     const int s = c % nst;
     const uint32_t dst = smem_u32(sA + s * STAGE_BYTES);
     mbar_expect_tx(full0 + 8 * s, a_bytes);
-    tma_load_2d(dst, tmA, c * TC_KC, a_row, full0 + 8 * s);
-    if constexpr (SPLIT) tma_load_2d(dst + A_BYTES, tmAlo, c * TC_KC, a_row, full0 + 8 * s);
+    for (int u = 0; u < mt; ++u) {
+      tma_load_2d(dst + u * A_BYTES, tmA, c * TC_KC, a_row + u * TC_M, full0 + 8 * s);
+      if constexpr (SPLIT) tma_load_2d(dst + (mt + u) * A_BYTES, tmAlo, c * TC_KC, a_row + u * TC_M, full0 + 8 * s);
+    }
   };
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmA)) : "memory");
@@ -419,18 +431,21 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
       const bool lo_zero = x_lo_zero && c < nX;
 #pragma unroll
       for (int k = 0; k < TC_KC / 16; ++k) {
-        const uint64_t ad = sw128_desc(a_addr + k * 32);
         const uint64_t bd = sw128_desc(b_addr + k * 32);
         const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
-        umma_bf16(tmem, ad, bd, IDESC, acc);
-        if constexpr (SPLIT) {
-          const uint64_t adl = sw128_desc(a_addr + A_BYTES + k * 32);
-          if (!lo_zero) {
-            const uint64_t bdl = sw128_desc(smem_u32(sBlo + c * BCH) + k * 32);
-            umma_bf16(tmem + NT, ad, bdl, IDESC, acc);
-            umma_bf16(tmem + NT, adl, bd, IDESC, 1u);
-          } else {
-            umma_bf16(tmem + NT, adl, bd, IDESC, acc);
+        for (int u = 0; u < mt; ++u) {
+          const uint32_t d = tmem + u * TPT;
+          const uint64_t ad = sw128_desc(a_addr + u * A_BYTES + k * 32);
+          umma_bf16(d, ad, bd, IDESC, acc);
+          if constexpr (SPLIT) {
+            const uint64_t adl = sw128_desc(a_addr + (mt + u) * A_BYTES + k * 32);
+            if (!lo_zero) {
+              const uint64_t bdl = sw128_desc(smem_u32(sBlo + c * BCH) + k * 32);
+              umma_bf16(d + NT, ad, bdl, IDESC, acc);
+              umma_bf16(d + NT, adl, bd, IDESC, 1u);
+            } else {
+              umma_bf16(d + NT, adl, bd, IDESC, acc);
+            }
           }
         }
       }
@@ -470,14 +485,17 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
   const int node = mv.L - 1 + leaf;
   const int ldo = (mv.kind == HM_HODLR) ? mv.Ke : mv.Kp;
   float* pout = static_cast<float*>(mv.kind == HM_HODLR ? ws.PS : ws.xh);
+  for (int u = 0; u < mt; ++u) {
+  const int tu = t0 + u * TC_M;                            // first row of tile u
+  const int nrows = lim - tu;                              // rows of tile u inside the output (may be <= 0)
   for (int cb = 0; cb < NT; cb += 16) {
     if constexpr (PROJ) {
       if (warp * 32 >= nrows) break;                       // whole warp outside the projection rows
     }
     float v[16];
-    tmem_ld16(lane_addr + cb, v);
+    tmem_ld16(lane_addr + u * TPT + cb, v);
     float w[16];
-    if constexpr (SPLIT) tmem_ld16(lane_addr + NT + cb, w);
+    if constexpr (SPLIT) tmem_ld16(lane_addr + u * TPT + NT + cb, w);
     if (done && row < nrows) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
@@ -485,9 +503,9 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
         if (col < r) {
           if constexpr (PROJ) {
             const float y = SPLIT ? v[j] + w[j] : v[j];
-            pout[(static_cast<int64_t>(node) * r + col) * ldo + t0 + row] = y;
+            pout[(static_cast<int64_t>(node) * r + col) * ldo + tu + row] = y;
           } else {
-            const int64_t idx = (a0 + t0 + row) + col * ldy;
+            const int64_t idx = (a0 + tu + row) + col * ldy;
             if constexpr (SPLIT) {
               const double y = static_cast<double>(v[j]) + static_cast<double>(w[j]);
               if (yt == HM_F64) static_cast<double*>(Y)[idx] = y;
@@ -501,6 +519,7 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
       }
     }
   }
+  }
   tc_fence_before();
   __syncthreads();
 }
@@ -510,24 +529,25 @@ __global__ void __launch_bounds__(128, 1)
     k_leaf_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmX, int use_tmx, int box_rows, MatView mv, Scratch ws, int64_t r,
               const void* X, int64_t ldx, int xt, void* Y, int64_t ldy, int yt, int tiles_per_leaf, int nK, int nX,
-              int nst) {
-  constexpr int NCOL = tc_ncols<SPLIT, NT>();
+              int nst, int mt) {
+  // tensor-memory columns: mt tiles of tc_ncols each (a power of two, at most 512)
+  const uint32_t NCOL = static_cast<uint32_t>(tc_ncols<SPLIT, NT>() * mt);
   pdl_launch_dependents();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw_s = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(base + tc_layout_bytes(SPLIT, NT, nK, nst) - 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(base + tc_layout_bytes(SPLIT, NT, nK, nst, mt) - 16);
   const int leaf = blockIdx.x / tiles_per_leaf;
   const int rt = blockIdx.x % tiles_per_leaf;
   const int lim = PROJ ? mv.Kp : static_cast<int>(mv.off[leaf + 1] - mv.off[leaf]);
-  if (rt * TC_M >= lim) return;
+  if (rt * TC_M * mt >= lim) return;
   if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(tslot), NCOL);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
   tc_tile<SPLIT, NT, PROJ>(&tmA, &tmAlo, use_tmx ? &tmX : nullptr, box_rows, mv, ws, r, X, ldx, xt, Y, ldy, yt,
-                           leaf, rt, blockIdx.y * NT, nK, nX, nst, base, tmem);
+                           leaf, rt, blockIdx.y * NT, nK, nX, nst, base, tmem, mt);
   if ((threadIdx.x >> 5) == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, NCOL);
