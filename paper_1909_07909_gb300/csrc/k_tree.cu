@@ -137,14 +137,16 @@ __device__ __forceinline__ void load_row(const C* __restrict__ v, C (&x)[RC]) {
   }
 }
 
-// Register tile of a warp task: lane (rb, cb) owns rows rb*RT .. rb*RT+RT-1
-// and columns cb*CT .. cb*CT+CT-1 of a 32 x RC output block, so a step j
-// reads one operator row (RT contiguous values per lane) and one vector row
-// (CT per lane) with few shared-memory wavefronts.
-template <int RC>
+// Register tile of a warp task over a group of CW of the RC columns (CW in
+// {1, 2, 4, 8}, CW <= RC): lane (rb, cb) owns rows rb*RT .. rb*RT+RT-1 and
+// columns cb*CT .. cb*CT+CT-1 of the group, so a step j reads one operator
+// row (RT contiguous values per lane) and one vector row (CT per lane) with
+// few shared-memory wavefronts.  Narrow groups give a level with few
+// products more warp tasks; every output's sum is the same whatever CW is.
+template <int CW>
 struct WTile {
-  static constexpr int CT = RC >= 2 ? 2 : 1;
-  static constexpr int RT = RC / CT;
+  static constexpr int CT = CW >= 2 ? 2 : 1;
+  static constexpr int RT = CW / CT;
   static constexpr int NRB = 32 / RT;   // row blocks per warp
 };
 
@@ -168,11 +170,12 @@ __device__ __forceinline__ void ld_vec(const C* __restrict__ p, C (&x)[N]) {
 }
 
 // acc[r][c] += sum over j < kj, in order, of M[j*ko + i0 + r] v[j][c0 + c]
-// (M, v in shared memory); groups of G steps load before they multiply.
-template <typename C, int RC>
+// (M, v in shared memory; v rows have RC values); groups of G steps load
+// before they multiply.
+template <typename C, int RC, int CW>
 __device__ __forceinline__ void tile_acc(const C* __restrict__ M, int ko, int kj, int i0, const C* __restrict__ v,
-                                         int c0, C (&acc)[WTile<RC>::RT][WTile<RC>::CT]) {
-  constexpr int RT = WTile<RC>::RT, CT = WTile<RC>::CT;
+                                         int c0, C (&acc)[WTile<CW>::RT][WTile<CW>::CT]) {
+  constexpr int RT = WTile<CW>::RT, CT = WTile<CW>::CT;
   constexpr int G = 8;
   int j = 0;
   for (; j + G <= kj; j += G) {
@@ -211,28 +214,27 @@ __device__ __forceinline__ void tile_acc(const C* __restrict__ M, int ko, int kj
   }
 }
 
-// One warp task: rows row0 .. row0+31 of out = M^T v (+ add) for all RC
-// columns, where row j of v is va[j] for j < ka and vb[j - ka] after (the
-// stacked children of R_V).  M and v in shared memory; out and add ([i][c]
-// blocks) in shared or global memory.  Split in two: wt_compute reads add
-// (before the sums, so a global read overlaps them) and the operands into
-// registers; wt_store writes the result, after the caller has released the
-// operator slot (so the release does not wait for these stores).  Rows come
-// in multiples of 8 (ko).
-template <typename C, int RC>
+// One warp task: rows row0 .. row0+31 and columns cg*CW .. cg*CW+CW-1 of
+// out = M^T v (+ add), where row j of v is va[j] for j < ka and vb[j - ka]
+// after (the stacked children of R_V).  M and v in shared memory; out and
+// add ([i][c] blocks of RC columns) in shared or global memory.  Split in
+// two: wt_compute reads add (before the sums, so a global read overlaps
+// them) and the operands into registers; wt_store writes the result, after
+// the caller has released the operator slot.  Rows come in multiples of 8.
+template <typename C, int CW>
 struct WTResult {
-  C acc[WTile<RC>::RT][WTile<RC>::CT];
+  C acc[WTile<CW>::RT][WTile<CW>::CT];
   int i0, c0;
   bool active;
 };
 
-template <typename C, int RC>
-__device__ __forceinline__ void wt_compute(WTResult<C, RC>& w, const C* M, int ko, int kj, const C* va, int ka,
-                                           const C* vb, const C* add, int row0) {
-  constexpr int RT = WTile<RC>::RT, CT = WTile<RC>::CT, NRB = WTile<RC>::NRB;
+template <typename C, int RC, int CW>
+__device__ __forceinline__ void wt_compute(WTResult<C, CW>& w, const C* M, int ko, int kj, const C* va, int ka,
+                                           const C* vb, const C* add, int row0, int cg) {
+  constexpr int RT = WTile<CW>::RT, CT = WTile<CW>::CT, NRB = WTile<CW>::NRB;
   const int lane = threadIdx.x & 31;
   w.i0 = row0 + (lane % NRB) * RT;
-  w.c0 = (lane / NRB) * CT;
+  w.c0 = cg * CW + (lane / NRB) * CT;
   w.active = w.i0 < ko;                  // ko is a multiple of 8, so rows i0 .. i0+RT-1 all exist
   if (!w.active) return;
   C a[RT][CT];
@@ -244,8 +246,8 @@ __device__ __forceinline__ void wt_compute(WTResult<C, RC>& w, const C* M, int k
   for (int r = 0; r < RT; ++r)
 #pragma unroll
     for (int c = 0; c < CT; ++c) w.acc[r][c] = C(0);
-  tile_acc<C, RC>(M, ko, ka < kj ? ka : kj, w.i0, va, w.c0, w.acc);
-  if (kj > ka) tile_acc<C, RC>(M + ka * ko, ko, kj - ka, w.i0, vb, w.c0, w.acc);
+  tile_acc<C, RC, CW>(M, ko, ka < kj ? ka : kj, w.i0, va, w.c0, w.acc);
+  if (kj > ka) tile_acc<C, RC, CW>(M + ka * ko, ko, kj - ka, w.i0, vb, w.c0, w.acc);
   if (add) {
 #pragma unroll
     for (int r = 0; r < RT; ++r)
@@ -254,9 +256,9 @@ __device__ __forceinline__ void wt_compute(WTResult<C, RC>& w, const C* M, int k
   }
 }
 
-template <typename C, int RC>
-__device__ __forceinline__ void wt_store(const WTResult<C, RC>& w, C* out) {
-  constexpr int RT = WTile<RC>::RT, CT = WTile<RC>::CT;
+template <typename C, int RC, int CW>
+__device__ __forceinline__ void wt_store(const WTResult<C, CW>& w, C* out) {
+  constexpr int RT = WTile<CW>::RT, CT = WTile<CW>::CT;
   if (!w.active) return;
 #pragma unroll
   for (int r = 0; r < RT; ++r)
@@ -291,9 +293,9 @@ __device__ void ring_issue(const Ring& R, const MatView& mv, int k) {
   const uint32_t bar = smem_u32(R.full + s);
   const int Kp = mv.Kp, Ke = mv.Ke;
   *R.issued = k + 1;
-  // the slot's barrier phase now belongs to item k: publish that before the copy
+  // the slot's barrier phase now belongs to item k (a reader that sees this
+  // before the expect_tx below still waits for the copy: the phase is open)
   *reinterpret_cast<volatile int*>(R.held + s) = k;
-  __threadfence_block();
   if (!down) {
     const uint32_t brv = static_cast<uint32_t>(2 * Kp * Kp) * sizeof(C);
     const uint32_t bb = static_cast<uint32_t>(Kp * Ke) * sizeof(C);
@@ -337,18 +339,22 @@ __device__ __forceinline__ void ring_acquire(const Ring& R, int k, int* err) {
 // slot requests item k + NS into it.
 template <typename C>
 __device__ __forceinline__ void ring_release(const Ring& R, const MatView& mv, int k) {
-  __syncwarp();
-  __threadfence_block();
+  __syncwarp();                                // every lane is done reading the slot
   if ((threadIdx.x & 31) == 0) {
     const int s = k % R.NS;
-    const int old = atomicAdd(R.cnt + s, 1);
+    // acquire-release: this warp's reads of the slot happen before the count,
+    // and the last reader sees every other reader's count
+    int old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.s32 %0, [%1], 1;"
+                 : "=r"(old)
+                 : "r"(smem_u32(R.cnt + s))
+                 : "memory");
     if (old + 1 > R.cons[k]) {                 // more readers than the item has: protocol broken
       atomicExch(R.err, 23);
       *(volatile int*)R.dead = 1;
     } else if (old + 1 == R.cons[k]) {
       R.cnt[s] = 0;
-      __threadfence_block();
-      fence_proxy_async();
+      fence_proxy_async();                     // the slot's generic reads before the copy that overwrites it
       if (!*(volatile int*)R.dead) ring_issue<C>(R, mv, k + R.NS);
     }
   }
@@ -401,6 +407,114 @@ __device__ __forceinline__ int level_perm(int t, int n) {
   return (t + rot) & (n - 1);
 }
 
+// Column-group width of a level with `tasks` full-width warp tasks.  Always
+// the full RC: narrower groups give idle warps work but keep each task's
+// dependent chain over j just as long, and multiply the slot handoffs
+// (measured slower on the small top levels), so they are not used.
+template <int RC>
+__device__ __forceinline__ int pick_cw(int tasks, int nwarps) {
+  (void)tasks;
+  (void)nwarps;
+  return RC;
+}
+
+enum { LV_UP = 0, LV_TOPUP = 1, LV_TOPDOWN = 2, LV_DOWN = 3 };
+
+// Everything a level's warp tasks need.
+template <typename C>
+struct LevelArgs {
+  int kind;
+  int k;              // first item of the level
+  int n;              // nodes (LV_UP), 1 (top), children (LV_DOWN)
+  int lev, first;     // level; first node (LV_UP) or first child (LV_DOWN) of the CTA's part
+  int nbp, nbe;       // 32-row blocks of the R_V and of the Ke-row outputs
+  int h;              // LV_TOPDOWN: child half
+  const C* cur;       // LV_UP: children x-hat; LV_TOPUP: stacked children; LV_TOPDOWN/DOWN: parent y-hat
+  C* out;             // LV_UP: x-hat of the level; LV_TOPUP: x-hat (TX); LV_TOPDOWN/DOWN: y-hat
+  C* tyc;             // LV_TOPUP: the two coupling outputs (TYC), LV_TOPDOWN: the coupling input
+  C* ycg;             // subtree couplings in scratch (node blocks of Ke x RC)
+  int VS;
+};
+
+// Runs the warp tasks of one level with column groups of CW: task w covers
+// product (w / ncg), column group (w % ncg), in item order per warp.
+template <typename C, int RC, int CW>
+__device__ void run_level(const Ring& R, const MatView& mv, int* err, const LevelArgs<C>& a) {
+  constexpr int ncg = RC / CW;
+  const int Kp = mv.Kp, Ke = mv.Ke;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int KeRC = Ke * RC;
+  int per;                                      // full-width tasks per item
+  int nitems_tasks;
+  if (a.kind == LV_UP || a.kind == LV_TOPUP) {
+    per = (a.lev > 0 ? a.nbp : 0) + 2 * a.nbe;
+    nitems_tasks = a.n * per;
+  } else if (a.kind == LV_TOPDOWN) {
+    per = a.nbe;
+    nitems_tasks = per;
+  } else {
+    per = 2 * a.nbe;                            // a parent's record serves both children
+    nitems_tasks = (a.n / 2) * per;
+  }
+  for (int w = warp; w < nitems_tasks * ncg; w += nwarps) {
+    const int cg = w % ncg;
+    const int tw = w / ncg;                     // full-width task
+    const int iu = tw / per;                    // item within the level
+    int b = tw % per;
+    const int item = a.k + iu;
+    ring_acquire(R, item, err);
+    const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(item % R.NS) * R.slot_bytes);
+    WTResult<C, CW> res;
+    C* dst;
+    if (a.kind == LV_UP || a.kind == LV_TOPUP) {
+      const int t = (a.kind == LV_UP) ? level_perm(iu, a.n) : 0;
+      const C* xa = a.cur + static_cast<size_t>(2 * t) * a.VS;
+      const C* xb = xa + a.VS;
+      if (a.lev > 0 && b < a.nbp) {
+        wt_compute<C, RC, CW>(res, op, Kp, 2 * Kp, xa, Kp, xb, nullptr, 32 * b, cg);
+        dst = a.out + static_cast<size_t>(t) * a.VS;
+      } else {
+        if (a.lev > 0) b -= a.nbp;
+        const int side = b < a.nbe ? 0 : 1;     // 0: B12 x-hat_b -> y_a, 1: B21 x-hat_a -> y_b
+        const int rb = side ? b - a.nbe : b;
+        wt_compute<C, RC, CW>(res, op + 2 * Kp * Kp + side * Kp * Ke, Ke, Kp, side ? xa : xb, Kp, side ? xa : xb,
+                              nullptr, 32 * rb, cg);
+        if (a.kind == LV_UP) dst = a.ycg + static_cast<int64_t>(2 * (a.first + t) + 1 + side) * KeRC;
+        else dst = a.tyc + static_cast<size_t>(side) * a.VS;
+      }
+    } else if (a.kind == LV_TOPDOWN) {
+      wt_compute<C, RC, CW>(res, op + a.h * Ke * Ke, Ke, Ke, a.cur, Ke, a.cur, a.tyc, 32 * b, cg);
+      dst = a.out;
+    } else {
+      const int u = level_perm(iu, a.n / 2);
+      const int hh = b / a.nbe;
+      b -= hh * a.nbe;
+      const int t = 2 * u + hh;
+      const C* yp = a.cur + static_cast<size_t>(u) * a.VS;
+      wt_compute<C, RC, CW>(res, op + hh * Ke * Ke, Ke, Ke, yp, Ke, yp,
+                            a.ycg + static_cast<int64_t>(a.first + t) * KeRC, 32 * b, cg);
+      dst = a.out + static_cast<size_t>(t) * a.VS;
+    }
+    ring_release<C>(R, mv, item);
+    wt_store<C, RC, CW>(res, dst);
+  }
+}
+
+template <typename C, int RC>
+__device__ void run_level_cw(const Ring& R, const MatView& mv, int* err, const LevelArgs<C>& a, int cw) {
+  if constexpr (RC >= 8) {
+    if (cw == 8) { run_level<C, RC, 8>(R, mv, err, a); return; }
+  }
+  if constexpr (RC >= 4) {
+    if (cw == 4) { run_level<C, RC, 4>(R, mv, err, a); return; }
+  }
+  if constexpr (RC >= 2) {
+    run_level<C, RC, 2>(R, mv, err, a);
+    return;
+  }
+  run_level<C, RC, 1>(R, mv, err, a);
+}
+
 template <typename C, int RC>
 __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Scratch ws, int64_t r, int NS, int S) {
   pdl_launch_dependents();
@@ -415,7 +529,6 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
   const int nleaf = 1 << d;
   const uint32_t V = vec_bytes<C>(T.K, RC);
   const int VS = T.K * RC;                   // elements per node vector
-  const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   C* A = reinterpret_cast<C*>(tree_smem + T.A);
   C* Bb = reinterpret_cast<C*>(tree_smem + T.B);
@@ -424,7 +537,6 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
   // downsweep of the same CTA
   const int64_t nodes = 2 * static_cast<int64_t>(mv.L) - 1;
   C* YCg = static_cast<C*>(ws.yf) + nodes * r * Ke + static_cast<int64_t>(blockIdx.y) * nodes * Ke * RC;
-  auto ycg = [&](int node) { return YCg + static_cast<int64_t>(node) * Ke * RC; };
   auto vec = [&](uint32_t off, int idx) {
     return reinterpret_cast<C*>(tree_smem + off + static_cast<size_t>(idx) * V);
   };
@@ -452,27 +564,34 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
     *R.issued = 0;
     if (hss) {
       int n = 0;
-      for (int lev = p - 1; lev >= s; --lev)                       // bottom upsweep
+      // consumers of an item: its full-width warp tasks times the level's column groups
+      for (int lev = p - 1; lev >= s; --lev) {                     // bottom upsweep
+        const int per = (lev > 0 ? nbp : 0) + 2 * nbe;
+        const int ncg = RC / pick_cw<RC>((1 << (lev - s)) * per, nwarps);
         for (int t = 0; t < (1 << (lev - s)); ++t) {
           items[n] = (1 << lev) - 1 + (j << (lev - s)) + level_perm(t, 1 << (lev - s));
-          cons[n++] = (lev > 0 ? nbp : 0) + 2 * nbe;
+          cons[n++] = per * ncg;
         }
+      }
       for (int lev = s - 1; lev >= 0; --lev)                       // top upsweep, owned nodes
         if ((j & ((1 << (s - lev)) - 1)) == 0) {
+          const int per = (lev > 0 ? nbp : 0) + 2 * nbe;
           items[n] = (1 << lev) - 1 + (j >> (s - lev));
-          cons[n++] = (lev > 0 ? nbp : 0) + 2 * nbe;
+          cons[n++] = per * (RC / pick_cw<RC>(per, nwarps));
         }
       for (int lev = 2; lev <= s; ++lev)                           // top downsweep: the parent's record
         if ((j & ((1 << (s - lev)) - 1)) == 0) {
           const int node = (1 << lev) - 1 + (j >> (s - lev));
           items[n] = (1 << 30) | ((node - 1) >> 1);
-          cons[n++] = nbe;
+          cons[n++] = nbe * (RC / pick_cw<RC>(nbe, nwarps));
         }
-      for (int lev = s + 1; lev <= p; ++lev)                       // bottom downsweep: parents
+      for (int lev = s + 1; lev <= p; ++lev) {                     // bottom downsweep: parents
+        const int ncg = RC / pick_cw<RC>((1 << (lev - s)) * nbe, nwarps);
         for (int u = 0; u < (1 << (lev - 1 - s)); ++u) {
           items[n] = (1 << 30) | ((1 << (lev - 1)) - 1 + (j << (lev - 1 - s)) + level_perm(u, 1 << (lev - 1 - s)));
-          cons[n++] = 2 * nbe;
+          cons[n++] = 2 * nbe * ncg;
         }
+      }
       items[TREE_MAX_ITEMS / 2 - 1] = n;
       for (int k = 0; k < T.NS; ++k) {
         mbar_init(smem_u32(R.full + k), 1);
@@ -503,33 +622,8 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
     const int nn = 1 << (lev - s);
     const int first = (1 << lev) - 1 + (j << (lev - s));
     if (hss) {
-      const int per = (lev > 0 ? nbp : 0) + 2 * nbe;
-      for (int w = warp; w < nn * per; w += nwarps) {
-        const int item = k + w / per;
-        const int t = level_perm(w / per, nn);
-        int b = w % per;
-        ring_acquire(R, item, ws.err);
-        const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(item % R.NS) * R.slot_bytes);
-        const C* xa = cur + static_cast<size_t>(2 * t) * VS;
-        const C* xb = xa + VS;
-        WTResult<C, RC> res;
-        C* dst;
-        if (lev > 0 && b < nbp) {
-          wt_compute<C, RC>(res, op, Kp, 2 * Kp, xa, Kp, xb, nullptr, 32 * b);
-          dst = nxt + static_cast<size_t>(t) * VS;
-        } else {
-          if (lev > 0) b -= nbp;
-          if (b < nbe) {
-            wt_compute<C, RC>(res, op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, nullptr, 32 * b);
-            dst = ycg(2 * (first + t) + 1);
-          } else {
-            wt_compute<C, RC>(res, op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, nullptr, 32 * (b - nbe));
-            dst = ycg(2 * (first + t) + 2);
-          }
-        }
-        ring_release<C>(R, mv, item);
-        wt_store<C, RC>(res, dst);
-      }
+      LevelArgs<C> la{LV_UP, k, nn, lev, first, nbp, nbe, 0, cur, nxt, nullptr, YCg, VS};
+      run_level_cw<C, RC>(R, mv, ws.err, la, pick_cw<RC>(nn * ((lev > 0 ? nbp : 0) + 2 * nbe), nwarps));
       k += nn;
     } else {
       // HODLR: T_q = T_a + T_b over the rows of levels 1..lev, written out for every node
@@ -570,31 +664,9 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
     if (own) {
       const int q = (1 << lev) - 1 + (j >> (s - lev));
       if (hss) {
-        const C* xa = ch;
-        const C* xb = ch + VS;
         const int per = (lev > 0 ? nbp : 0) + 2 * nbe;
-        for (int w = warp; w < per; w += nwarps) {
-          int b = w;
-          ring_acquire(R, k, ws.err);
-          const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(k % R.NS) * R.slot_bytes);
-          WTResult<C, RC> res;
-          C* dst;
-          if (lev > 0 && b < nbp) {
-            wt_compute<C, RC>(res, op, Kp, 2 * Kp, xa, Kp, xb, nullptr, 32 * b);
-            dst = vec(T.TX, lev);
-          } else {
-            if (lev > 0) b -= nbp;
-            if (b < nbe) {
-              wt_compute<C, RC>(res, op + 2 * Kp * Kp, Ke, Kp, xb, Kp, xb, nullptr, 32 * b);
-              dst = vec(T.TYC, 2 * lev);
-            } else {
-              wt_compute<C, RC>(res, op + 2 * Kp * Kp + Kp * Ke, Ke, Kp, xa, Kp, xa, nullptr, 32 * (b - nbe));
-              dst = vec(T.TYC, 2 * lev + 1);
-            }
-          }
-          ring_release<C>(R, mv, k);
-          wt_store<C, RC>(res, dst);
-        }
+        LevelArgs<C> la{LV_TOPUP, k, 1, lev, q, nbp, nbe, 0, ch, vec(T.TX, lev), vec(T.TYC, 2 * lev), YCg, VS};
+        run_level_cw<C, RC>(R, mv, ws.err, la, pick_cw<RC>(per, nwarps));
         ++k;
       } else {
         const int rows = mv.koff[lev + 1];
@@ -630,14 +702,8 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
         if (lev == 1) {
           for (int u = threadIdx.x; u < VS; u += blockDim.x) yf[u] = syc[u];
         } else {
-          for (int w = warp; w < nbe; w += nwarps) {
-            ring_acquire(R, k, ws.err);
-            const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(k % R.NS) * R.slot_bytes);
-            WTResult<C, RC> res;
-            wt_compute<C, RC>(res, op + h * Ke * Ke, Ke, Ke, syp, Ke, syp, syc, 32 * w);
-            ring_release<C>(R, mv, k);
-            wt_store<C, RC>(res, yf);
-          }
+          LevelArgs<C> la{LV_TOPDOWN, k, 1, lev, node, nbp, nbe, h, syp, yf, syc, YCg, VS};
+          run_level_cw<C, RC>(R, mv, ws.err, la, pick_cw<RC>(nbe, nwarps));
           ++k;
         }
       }
@@ -649,20 +715,8 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
       const int nc = 1 << (lev - s);                              // children at lev
       C* out = ((p - lev) % 2 == 0) ? A : Bb;
       const int firstc = (1 << lev) - 1 + (j << (lev - s));
-      for (int w = warp; w < nc * nbe; w += nwarps) {
-        const int b = w % nbe;
-        const int uu = (w / nbe) >> 1, hh = (w / nbe) & 1;
-        const int item = k + uu;
-        const int u = level_perm(uu, nc / 2);
-        const int t = 2 * u + hh;
-        ring_acquire(R, item, ws.err);
-        const C* op = reinterpret_cast<const C*>(R.slots + static_cast<size_t>(item % R.NS) * R.slot_bytes);
-        const C* yp = ypar + static_cast<size_t>(u) * VS;
-        WTResult<C, RC> res;
-        wt_compute<C, RC>(res, op + hh * Ke * Ke, Ke, Ke, yp, Ke, yp, ycg(firstc + t), 32 * b);
-        ring_release<C>(R, mv, item);
-        wt_store<C, RC>(res, out + static_cast<size_t>(t) * VS);
-      }
+      LevelArgs<C> la{LV_DOWN, k, nc, lev, firstc, nbp, nbe, 0, ypar, out, nullptr, YCg, VS};
+      run_level_cw<C, RC>(R, mv, ws.err, la, pick_cw<RC>(nc * nbe, nwarps));
       k += nc / 2;
       __syncthreads();
       if (lev == p) {
