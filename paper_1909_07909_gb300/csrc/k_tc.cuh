@@ -55,12 +55,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// One test of an mbarrier phase; the thread is suspended (not spinning)
+// until the phase completes or about 1 us passes.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(1000u)
       : "memory");
   return ok != 0;
 }
@@ -478,7 +480,10 @@ __device__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmAlo, const 
     fence_proxy_async();
     asm volatile("bar.arrive 1, 128;" ::: "memory");
   }
-  const bool done = mbar_wait(accb, 0, err, 13);
+  // one lane per warp waits for the accumulators; the rest of the warp waits at the warp barrier
+  int done_i = 0;
+  if (lane == 0) done_i = mbar_wait(accb, 0, err, 13) ? 1 : 0;
+  const bool done = __shfl_sync(0xffffffffu, done_i, 0) != 0;
   tc_fence_after();
   const int row = warp * 32 + lane;
   const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
