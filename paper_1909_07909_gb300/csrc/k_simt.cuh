@@ -827,7 +827,17 @@ hm_status launch_phase_rc(int phase, const MatView& mv, const Scratch& ws, int64
                  nchunks);
     prof_mark(ws.prof, 0, false, st);
   } else {
-    const int RT = 64;
+    // rows per block: a whole leaf (up to 256 rows) when that still gives
+    // several blocks per SM, so a block's fixed work (staging X and Z,
+    // barriers) is spread over more streamed rows; the row sums do not depend
+    // on it
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int RT = 64;
+    while (RT < 256 && RT < mv.m_pad &&
+           static_cast<int64_t>(mv.L) * ((mv.m_pad + 2 * RT - 1) / (2 * RT)) * nchunks >= 4 * sms)
+      RT *= 2;
     const int tiles = (mv.m_pad + RT - 1) / RT;
     const size_t smem = sizeof(C) * static_cast<size_t>(RC * mv.We + RC * (RT + 1));
     if (smem > 220 * 1024) return HM_EUNSUPPORTED;
