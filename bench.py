@@ -66,6 +66,32 @@ def dist_env():
         int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def rank_barrier(world):
+    """All ranks meet (no-op for one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ms_local, world, device):
+    """The whole job's timed region: the longest rank's (a MAX all-reduce,
+    then a barrier); `device` is where the reduction tensor lives ("cuda" for
+    NCCL, "cpu" for gloo)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(bytes_per_step, steps, ms_max, world):
+    """Whole-job GB/s: every rank runs `steps` products of `bytes_per_step`
+    (weak scaling) within the longest rank's `ms_max`."""
+    return world * bytes_per_step * steps / (ms_max * 1e-3) / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -188,7 +214,7 @@ def tree_flops(c):
 
 
 def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases, clock_index=None,
-                 prof_steps=None):
+                 prof_steps=None, world=1):
     """Device throughput of one storage type (timed region without profiling
     events, so consecutive kernels overlap), then a profiled pass that brackets
     every kernel with CUDA events for per-kernel durations."""
@@ -218,11 +244,14 @@ def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases
     if sampler:
         sampler.__enter__()
     torch.cuda.synchronize()
+    rank_barrier(world)
+    torch.cuda.synchronize()
     e0.record(stream)
     for i in range(steps):
         run(i)
     e1.record(stream)
     torch.cuda.synchronize()
+    rank_barrier(world)
     if sampler:
         sampler.__exit__()
     ms_total = e0.elapsed_time(e1)
@@ -574,14 +603,10 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     head, Yh = time_variant(hm, torch, tree, g, prec, args.steps, args.warmup, copies, True,
-                            clock_index=local, prof_steps=min(args.steps, 200))
+                            clock_index=local, prof_steps=min(args.steps, 200), world=world)
     # whole-job time: max over ranks of this rank's timed region
-    t_local = torch.tensor([head["ms_total"]], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-    ms_max = float(t_local.item())
-    value = world * head["bytes_per_step"] * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(head["ms_total"], world, "cuda")
+    value = job_throughput(head["bytes_per_step"], args.steps, ms_max, world)
 
     # dominant kernel roofline (per-kernel durations from the profiled pass)
     pb = phase_bytes(prec, c)
