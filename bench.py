@@ -560,9 +560,15 @@ def run_serve(args):
         torch.cuda.synchronize()
         f64.append((time.perf_counter() - t0) / 5)
     f64_ms = 1e3 * float(np.mean(f64))
-    top = by_rate[str(max(rates))]
+    # headline: the p99 latency at the highest offered rate the server sustains
+    # (completes at least 95 % of what is offered); also the saturation throughput
+    sustained = [rt for rt in rates if by_rate[str(rt)]["throughput_rps"] >= 0.95 * rt]
+    top_rate = max(sustained) if sustained else min(rates)
+    top = by_rate[str(top_rate)]
     out = {"metric": METRIC, "value": top["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "steps": len(rates),
            "warmup": 0, "ms_per_step": top["p50_ms"], "higher_is_better": False, "scaling": "weak",
+           "sustained_rps": top_rate,
+           "saturation_throughput_rps": max(v["throughput_rps"] for v in by_rate.values()),
            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
            "config": {"workload": "serving %d resident HSS matrices n=2^12..2^18 rank 16..64 BF16, Poisson "
                                   "arrivals, 1..16 RHS per request, 100 GB budget" % count},
