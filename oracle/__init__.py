@@ -21,6 +21,8 @@ define, so the oracle is that definition written out in float64:
                   two-pass recurrence (full-vector reference at any n).
 * ``bounds``   -- the componentwise forward-error envelope
                   ``|D||X| + sum |U|(|V|^T |X|)`` (HSS: with |R| and |S|).
+* ``transpose``-- generators of A^T by the block definition
+                  (A^T)(I, J) = A(J, I)^T and the product Y = A^T X.
 * ``fig41``    -- the recursive HODLR product and the four-step HSS product of
                   Fig. 4.1, kept only to show which reading of the printed
                   coupling loop agrees with the definition.
@@ -29,4 +31,4 @@ Every function is pinned by ``tests/test_oracle_*.py`` against brute force,
 closed forms and exact-rank fixtures; none is "parity unpinned".
 """
 
-from . import tree, dense, matmat, expkernel, bounds, fig41  # noqa: F401
+from . import tree, dense, matmat, expkernel, bounds, fig41, transpose  # noqa: F401

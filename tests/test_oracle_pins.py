@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import bounds, dense, expkernel, fig41, matmat as M, tree as T
+from oracle import bounds, dense, expkernel, fig41, matmat as M, transpose as TR, tree as T
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -442,3 +442,102 @@ def test_planted_mistakes(monkeypatch, plant):
                             lambda c_, g_: orig(c_, dict(g_, U21=g_["V21"], V21=g_["U21"])))
     A = dense.dense(c, g)
     assert not np.allclose(A, ref, rtol=1e-6, atol=1e-6), plant
+
+
+# --------------------------------------------------------------------------
+# Transposed product (A^T X; products with A^* in Sec. 3.2-3.3, Table 3.1)
+# --------------------------------------------------------------------------
+
+def _mixed_gens(kind, c, seed):
+    """Per-node ranks that differ between rows and columns (ku != kv), so a
+    swapped pair of factors cannot pass by symmetry."""
+    rng = np.random.default_rng(seed)
+    if kind == "hodlr":
+        return W.random_hodlr(rng, c, lambda q: (1 + q % 3, 2 + q % 2))
+    return W.random_hss(rng, c, lambda q: (1 + q % 4, 1 + (q * 7) % 3), orthonormal=False)
+
+
+@pytest.mark.parametrize("kind", ["hodlr", "hss"])
+@pytest.mark.parametrize("name,c", SMALL_TREES + [("variable_p3", T.default_leaf_ends(40, 5))])
+def test_transpose_gens_brute_force(kind, name, c):
+    """Every entry of the relabelled generators, evaluated on its own, is the
+    mirrored entry of A."""
+    g = _mixed_gens(kind, c, 17)
+    gt = TR.transpose_gens(c, g)
+    assert np.allclose(brute_dense(c, gt), brute_dense(c, g).T, rtol=1e-13, atol=1e-13), name
+
+
+@pytest.mark.parametrize("kind", ["hodlr", "hss"])
+def test_transpose_adjoint_identity(kind):
+    """<Z, A X> = <A^T Z, X> through the streamed products."""
+    c = T.default_leaf_ends(90, 7)
+    g = _mixed_gens(kind, c, 23)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((90, 3))
+    Z = rng.standard_normal((90, 2))
+    lhs = Z.T @ M.matmat(c, g, X)
+    rhs = TR.matmat_transpose(c, g, Z).T @ X
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+    idx = [0, 45, 89]
+    assert np.allclose(TR.matmat_transpose_rows(c, g, Z, idx), TR.matmat_transpose(c, g, Z)[idx],
+                       rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["hodlr", "hss"])
+def test_transpose_is_an_involution(kind):
+    c = T.default_leaf_ends(40, 5)
+    g = _mixed_gens(kind, c, 29)
+    gtt = TR.transpose_gens(c, TR.transpose_gens(c, g))
+    for key, blocks in g.items():
+        if key == "kind":
+            continue
+        for a, b in zip(blocks, gtt[key]):
+            assert (a is None and b is None) or np.array_equal(np.asarray(a), np.asarray(b)), key
+
+
+@pytest.mark.parametrize("fmt", ["hodlr", "hss"])
+def test_transpose_of_symmetric_closed_form(fmt):
+    """T^{-1} of tridiag(-1, 2, -1) is symmetric: A^T X = A X (closed form,
+    min(i,j)(n+1-max(i,j))/(n+1))."""
+    n = 77
+    c = T.default_leaf_ends(n, 9)
+    g = W.tridiag_inverse_hodlr(c) if fmt == "hodlr" else W.tridiag_inverse_hss(c)
+    X = np.random.default_rng(6).standard_normal((n, 2))
+    i = np.arange(1, n + 1)
+    Tinv = np.minimum.outer(i, i) * (n + 1 - np.maximum.outer(i, i)) / (n + 1)
+    assert np.allclose(TR.matmat_transpose(c, g, X), Tinv @ X, rtol=1e-12, atol=1e-12)
+
+
+def _bad_transpose(plant):
+    orig = TR.transpose_gens
+
+    def bad(c_, g_):
+        gt = orig(c_, g_)
+        if plant == "hss_b12_not_b21":
+            gt["B12"] = [np.asfortranarray(B.T) for B in g_["B12"]]
+        elif plant == "hss_ru_kept":
+            gt["RU"] = list(g_["RU"])
+        elif plant == "hss_untransposed_coupling":
+            gt["B12"] = list(g_["B21"])
+        elif plant == "hodlr_u12_from_v12":
+            gt["U12"] = list(g_["V12"])
+        elif plant == "leaf_d_kept":
+            gt["D"] = list(g_["D"])
+        return gt
+    return bad
+
+
+@pytest.mark.parametrize("plant", ["hss_b12_not_b21", "hss_ru_kept", "hss_untransposed_coupling",
+                                   "hodlr_u12_from_v12", "leaf_d_kept"])
+def test_transpose_planted_mistakes(monkeypatch, plant):
+    c = [6, 12, 18, 24, 30, 36, 42, 48]
+    kind = "hodlr" if plant.startswith("hodlr") else "hss"
+    rng = np.random.default_rng(37)
+    if kind == "hodlr":
+        g = W.random_hodlr(rng, c, 3)
+    else:
+        g = W.random_hss(rng, c, 3, orthonormal=False)
+    ref = brute_dense(c, g).T
+    monkeypatch.setattr(TR, "transpose_gens", _bad_transpose(plant))
+    got = brute_dense(c, TR.transpose_gens(c, g))
+    assert not np.allclose(got, ref, rtol=1e-6, atol=1e-6), plant
