@@ -214,14 +214,19 @@ def tree_flops(c):
 
 
 def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases, clock_index=None,
-                 prof_steps=None, world=1):
+                 prof_steps=None, world=1, transpose=False):
     """Device throughput of one storage type (timed region without profiling
     events, so consecutive kernels overlap), then a profiled pass that brackets
-    every kernel with CUDA events for per-kernel durations."""
+    every kernel with CUDA events for per-kernel durations.  transpose=True
+    times Y = A^T X (matrices from hm_matrix_transpose)."""
     td = torch.float64 if storage == "f64" else torch.float32
     xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
     dev = torch.device("cuda", torch.cuda.current_device())
-    mats = [hm.Matrix.create(tree, g, storage) for _ in range(copies)]
+    mats = []
+    for _ in range(copies):
+        A0 = hm.Matrix.create(tree, g, storage)
+        mats.append(A0.transpose() if transpose else A0)
+        del A0
     Xh = torch.from_numpy(g["_X"].T.copy())
     Xs = [Xh.to(dev).to(xd).t() for _ in range(copies)]
     Ys = [torch.empty((RHS, N_), dtype=td, device=dev).t() for _ in range(copies)]
@@ -679,7 +684,23 @@ def main():
                                                      for k in range(4)}}
                 if pbv[PHASES[d]]:
                     variants[v]["dominant_gbs"] = pbv[PHASES[d]] / (am * 1e-3) / 1e9
+            # the transposed product A^T X on the headline storage
+            st = max(20, args.steps // 4)
+            r_, yt = time_variant(hm, torch, tree, g, prec, st, 3, copies, True, prof_steps=min(st, 20),
+                                  transpose=True)
+            d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
+            variants["transpose"] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
+                                     "storage": prec, "dominant_kernel": PHASES[d],
+                                     "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
+                                                           for k in range(4)}}
         if not args.no_cpu and world == 1:
+            if "transpose" in variants:
+                from oracle import transpose as OTR
+                trows = sorted(set([0, N_ - 1] + list(range(255, N_, N_ // 190))))[:192]
+                Yt_o = OTR.matmat_transpose_rows(c, g, X, trows)
+                variants["transpose"]["err_vs_oracle"] = float(np.max(
+                    np.linalg.norm(yt[trows] - Yt_o, axis=0) / np.linalg.norm(Yt_o, axis=0)))
+                variants["transpose"]["err_rows"] = len(trows)
             leaves = [0, 1, 127, 128, 200, 255][: max(1, args.cpu_leaves)]
             dt, rows, Yo = cpu_oracle_sample(c, g, X, leaves)
             frac = len(leaves) / len(c)
@@ -697,7 +718,8 @@ def main():
             out["err_vs_oracle"] = {"metric": "max over columns of ||y - y_oracle||_2/||y_oracle||_2 on %d sampled rows"
                                               % len(rows), **errs}
             for v in variants:
-                variants[v]["err_vs_oracle"] = errs.get(v)
+                if v in errs:
+                    variants[v]["err_vs_oracle"] = errs[v]
         if variants:
             out["variants"] = variants
             if "f64" in variants and prec != "f64":

@@ -149,7 +149,7 @@ typedef struct {
   int32_t depth;         /* p */
   int32_t num_leaves;    /* 2^p */
   int32_t leaf_pad;      /* padded leaf width used by the kernels */
-  int32_t rank_total;    /* HODLR: sum over levels of the padded ranks; HSS: padded rank */
+  int32_t rank_total;    /* HODLR: sum over levels of the padded ranks; HSS: padded row-basis (U) rank */
   int64_t generator_elements;  /* unpadded count: HODLR n m + 2 n k p; HSS as Sec. 2.2 */
   size_t  generator_bytes;     /* algorithmic bytes of the generators in `storage` */
   size_t  device_bytes;        /* bytes the library holds on the device for A */
@@ -157,12 +157,31 @@ typedef struct {
                                   one-launch tree kernel, 0 = per-level kernels (or none yet) */
   int32_t tree_columns;        /* right-hand-side columns per cluster (0 likewise) */
   int32_t tree_ring;           /* operator ring slots per CTA (HSS; 0 likewise or HODLR) */
+  int32_t rank_col;            /* HSS: padded column-basis (V) rank; HODLR: rank_total */
 } hm_matrix_info_t;
 
 hm_status hm_matrix_info(const hm_matrix* A, hm_matrix_info_t* out);
 
 /* Algorithmic generator bytes (the figure a roofline divides by time). */
 hm_status hm_matrix_bytes(const hm_matrix* A, size_t* bytes);
+
+/* A^T as a new matrix of the same kind, tree and storage type, built on the
+ * current device from A's device storage (products with A^* next to products
+ * with A: the constructors of Sec. 3.2-3.3, Table 3.1; real data, so A^T).
+ * The generators are relabelled block by block, (A^T)(I, J) = A(J, I)^T:
+ * D_i -> D_i^T; HODLR (Def. 2.2) U12' = V21, V12' = U21, U21' = V12,
+ * V21' = U12; HSS (Def. 2.3, Eq. 2.2) U' = V, V' = U, R_U' = R_V,
+ * R_V' = R_U, B12' = B21^T, B21' = B12^T.  Every stored value is copied, not
+ * recomputed, so A^T holds A's values exactly in every storage type and the
+ * transpose of the result is A bit for bit.  Products with the result go
+ * through hm_hodlr_matmat / hm_hss_matmat like any other matrix.
+ * Ownership: *out is a new handle owned by the caller (hm_destroy); A is not
+ * modified and may be destroyed first.  Memory: as much device memory as A.
+ * Synchronous (runs on the legacy default stream and waits for it).
+ * Errors: HM_EINVAL for a NULL out, a handle that is not a matrix, or a
+ * current device other than A's; HM_ENOMEM when device memory runs out;
+ * HM_ECUDA for another CUDA error.  *out is NULL on any error. */
+hm_status hm_matrix_transpose(const hm_matrix* A, hm_matrix** out);
 
 /* Reserves device scratch for products with up to r_max right-hand sides so
  * that later calls allocate nothing (needed before CUDA-graph capture).

@@ -44,7 +44,7 @@ class hm_matrix_info_t(C.Structure):
                 ("num_leaves", C.c_int32), ("leaf_pad", C.c_int32), ("rank_total", C.c_int32),
                 ("generator_elements", C.c_int64), ("generator_bytes", C.c_size_t),
                 ("device_bytes", C.c_size_t), ("tree_cluster", C.c_int32), ("tree_columns", C.c_int32),
-                ("tree_ring", C.c_int32)]
+                ("tree_ring", C.c_int32), ("rank_col", C.c_int32)]
 
 
 class hm_batch_info_t(C.Structure):
@@ -81,6 +81,7 @@ _decl("hm_hodlr_create", C.c_int, vp, C.POINTER(hm_hodlr_gens), C.c_int, C.POINT
 _decl("hm_hss_create", C.c_int, vp, C.POINTER(hm_hss_gens), C.c_int, C.POINTER(vp))
 _decl("hm_matrix_info", C.c_int, vp, C.POINTER(hm_matrix_info_t))
 _decl("hm_matrix_bytes", C.c_int, vp, C.POINTER(C.c_size_t))
+_decl("hm_matrix_transpose", C.c_int, vp, C.POINTER(vp))
 _decl("hm_matrix_reserve", C.c_int, vp, C.c_int64)
 _decl("hm_matrix_set_path", C.c_int, vp, C.c_int32)
 _decl("hm_matrix_set_tree", C.c_int, vp, C.c_int32)

@@ -157,6 +157,13 @@ class Matrix:
         check(lib.hm_matrix_bytes(self._h, C.byref(b)), "hm_matrix_bytes")
         return b.value
 
+    def transpose(self):
+        """A^T as a new matrix on the same device (generators relabelled in
+        device memory; values copied exactly)."""
+        h = vp()
+        check(lib.hm_matrix_transpose(self._h, C.byref(h)), "hm_matrix_transpose")
+        return Matrix(h, self.kind, self.tree)
+
     def reserve(self, r_max):
         check(lib.hm_matrix_reserve(self._h, int(r_max)), "hm_matrix_reserve")
 

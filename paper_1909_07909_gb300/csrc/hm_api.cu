@@ -570,6 +570,7 @@ extern "C" hm_status hm_matrix_info(const hm_matrix* A, hm_matrix_info_t* out) {
   out->tree_cluster = cl ? (1 << A->tree_s) : 0;
   out->tree_columns = cl ? A->tree_rc : 0;
   out->tree_ring = cl ? A->tree_ns : 0;
+  out->rank_col = A->Kp;
   return HM_OK;
 }
 
