@@ -23,6 +23,8 @@ define, so the oracle is that definition written out in float64:
                   ``|D||X| + sum |U|(|V|^T |X|)`` (HSS: with |R| and |S|).
 * ``transpose``-- generators of A^T by the block definition
                   (A^T)(I, J) = A(J, I)^T and the product Y = A^T X.
+* ``convert``  -- hss2hodlr (Sec. 3.5): HODLR generators of an HSS matrix from
+                  its explicit nested bases.
 * ``fig41``    -- the recursive HODLR product and the four-step HSS product of
                   Fig. 4.1, kept only to show which reading of the printed
                   coupling loop agrees with the definition.
@@ -31,4 +33,4 @@ Every function is pinned by ``tests/test_oracle_*.py`` against brute force,
 closed forms and exact-rank fixtures; none is "parity unpinned".
 """
 
-from . import tree, dense, matmat, expkernel, bounds, fig41, transpose  # noqa: F401
+from . import tree, dense, matmat, expkernel, bounds, fig41, transpose, convert  # noqa: F401

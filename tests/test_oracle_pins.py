@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import bounds, dense, expkernel, fig41, matmat as M, transpose as TR, tree as T
+from oracle import bounds, convert as CV, dense, expkernel, fig41, matmat as M, transpose as TR, tree as T
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -540,4 +540,56 @@ def test_transpose_planted_mistakes(monkeypatch, plant):
     ref = brute_dense(c, g).T
     monkeypatch.setattr(TR, "transpose_gens", _bad_transpose(plant))
     got = brute_dense(c, TR.transpose_gens(c, g))
+    assert not np.allclose(got, ref, rtol=1e-6, atol=1e-6), plant
+
+
+# --------------------------------------------------------------------------
+# hss2hodlr (Sec. 3.5)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,c", SMALL_TREES + [("variable_p3", T.default_leaf_ends(40, 5))])
+def test_hss_to_hodlr_brute_force(name, c):
+    """Every entry of the converted HODLR generators, evaluated on its own,
+    equals the HSS entry (rank per node differs between rows and columns)."""
+    g = _mixed_gens("hss", c, 41)
+    h = CV.hss_to_hodlr(c, g)
+    assert np.allclose(brute_dense(c, h), brute_dense(c, g), rtol=1e-13, atol=1e-13), name
+    L = len(c)
+    for q in range(L - 1):
+        a, b = T.children(q)
+        kv = lambda x: (np.asarray(g["V"][x - (L - 1)]).shape[1] if x >= L - 1 else g["RV"][x].shape[1])
+        assert h["U12"][q].shape[1] == kv(b) and h["U21"][q].shape[1] == kv(a)
+
+
+def test_hss_to_hodlr_products_and_rejects_hodlr():
+    c = T.default_leaf_ends(120, 9)
+    g = _mixed_gens("hss", c, 43)
+    X = np.random.default_rng(8).standard_normal((120, 4))
+    assert np.allclose(M.matmat(c, CV.hss_to_hodlr(c, g), X), M.matmat(c, g, X), rtol=1e-12, atol=1e-12)
+    with pytest.raises(ValueError):
+        CV.hss_to_hodlr(c, _mixed_gens("hodlr", c, 1))
+
+
+@pytest.mark.parametrize("plant", ["b12_for_b21", "v_from_wrong_child", "rv_in_row_bases"])
+def test_hss_to_hodlr_planted_mistakes(monkeypatch, plant):
+    c = [6, 12, 18, 24, 30, 36, 42, 48]
+    g = W.random_hss(np.random.default_rng(47), c, 3, orthonormal=False)
+    ref = brute_dense(c, g)
+    orig = CV.hss_to_hodlr
+
+    def bad(c_, g_):
+        h = orig(c_, g_)
+        Ub, Vb = dense.hss_bases(c_, g_)
+        for q in range(len(c_) - 1):
+            a, b = T.children(q)
+            if plant == "b12_for_b21":
+                h["U21"][q] = Ub[b] @ g_["B12"][q].T
+            elif plant == "v_from_wrong_child":
+                h["V12"][q] = Vb[a] if Vb[a].shape == Vb[b].shape else h["V12"][q]
+            elif plant == "rv_in_row_bases":
+                Uw, _ = dense.hss_bases(c_, dict(g_, RU=g_["RV"]))
+                h["U12"][q] = Uw[a] @ g_["B12"][q]
+        return h
+    monkeypatch.setattr(CV, "hss_to_hodlr", bad)
+    got = brute_dense(c, CV.hss_to_hodlr(c, g))
     assert not np.allclose(got, ref, rtol=1e-6, atol=1e-6), plant
