@@ -214,18 +214,19 @@ def tree_flops(c):
 
 
 def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases, clock_index=None,
-                 prof_steps=None, world=1, transpose=False):
+                 prof_steps=None, world=1, form=None):
     """Device throughput of one storage type (timed region without profiling
     events, so consecutive kernels overlap), then a profiled pass that brackets
-    every kernel with CUDA events for per-kernel durations.  transpose=True
-    times Y = A^T X (matrices from hm_matrix_transpose)."""
+    every kernel with CUDA events for per-kernel durations.  form="transpose"
+    times Y = A^T X (matrices from hm_matrix_transpose); form="hodlr" times
+    the HODLR form of the HSS matrix (hm_hss_to_hodlr)."""
     td = torch.float64 if storage == "f64" else torch.float32
     xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
     dev = torch.device("cuda", torch.cuda.current_device())
     mats = []
     for _ in range(copies):
         A0 = hm.Matrix.create(tree, g, storage)
-        mats.append(A0.transpose() if transpose else A0)
+        mats.append(A0.transpose() if form == "transpose" else A0.to_hodlr() if form == "hodlr" else A0)
         del A0
     Xh = torch.from_numpy(g["_X"].T.copy())
     Xs = [Xh.to(dev).to(xd).t() for _ in range(copies)]
@@ -687,12 +688,22 @@ def main():
             # the transposed product A^T X on the headline storage
             st = max(20, args.steps // 4)
             r_, yt = time_variant(hm, torch, tree, g, prec, st, 3, copies, True, prof_steps=min(st, 20),
-                                  transpose=True)
+                                  form="transpose")
             d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
             variants["transpose"] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
                                      "storage": prec, "dominant_kernel": PHASES[d],
                                      "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
                                                            for k in range(4)}}
+            # the same matrix in HODLR form (hss2hodlr on the device): more bytes, no tree recursion
+            r_, yh = time_variant(hm, torch, tree, g, prec, st, 3, copies, True, prof_steps=min(st, 20),
+                                  form="hodlr")
+            ys["hodlr_from_hss"] = yh
+            d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
+            variants["hodlr_from_hss"] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
+                                          "storage": prec, "generator_bytes": r_["generator_bytes"],
+                                          "dominant_kernel": PHASES[d],
+                                          "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] /
+                                                                r_["phases"]["steps"] for k in range(4)}}
         if not args.no_cpu and world == 1:
             if "transpose" in variants:
                 from oracle import transpose as OTR

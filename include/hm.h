@@ -183,6 +183,26 @@ hm_status hm_matrix_bytes(const hm_matrix* A, size_t* bytes);
  * HM_ECUDA for another CUDA error.  *out is NULL on any error. */
 hm_status hm_matrix_transpose(const hm_matrix* A, hm_matrix** out);
 
+/* The HODLR form of an HSS matrix (hss2hodlr, Sec. 3.5) as a new HODLR matrix
+ * on the current device, built from S's device storage.  With the nested
+ * bases of Eq. 2.2 written out for every node, the sibling blocks of
+ * Def. 2.3 give the HODLR factors of Def. 2.2: U12 = U_a B12, V12 = V_b,
+ * U21 = U_b B21, V21 = V_a; the diagonal blocks are copied.  Arithmetic is in
+ * the type of S's translation operators (float64 for HM_F64 storage, float32
+ * otherwise); every factor is rounded once to S's storage type (HM_BF16X2:
+ * hi and lo of the float32 value), so for reduced storage the result differs
+ * from S by that rounding.  Every level of the result has S's padded column
+ * rank, so its rank_total is p times that rank and it holds about
+ * (m + 2 p k) n elements against S's (m + 2 k) n.
+ * Ownership: *out is a new handle owned by the caller (hm_destroy); S is not
+ * modified.  Synchronous (legacy default stream).
+ * Errors: HM_EINVAL for a NULL out, a handle that is not an HSS matrix, or a
+ * current device other than S's; HM_EUNSUPPORTED when the ranks need more
+ * than 200 KB of shared memory per block (16 (Ke + Kp) elements);
+ * HM_ENOMEM / HM_ECUDA for allocation and other CUDA failures.  *out is NULL
+ * on any error. */
+hm_status hm_hss_to_hodlr(const hm_matrix* S, hm_matrix** out);
+
 /* Reserves device scratch for products with up to r_max right-hand sides so
  * that later calls allocate nothing (needed before CUDA-graph capture).
  * Synchronous. */

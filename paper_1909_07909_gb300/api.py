@@ -164,6 +164,12 @@ class Matrix:
         check(lib.hm_matrix_transpose(self._h, C.byref(h)), "hm_matrix_transpose")
         return Matrix(h, self.kind, self.tree)
 
+    def to_hodlr(self):
+        """The HODLR form of this HSS matrix (hss2hodlr) as a new matrix."""
+        h = vp()
+        check(lib.hm_hss_to_hodlr(self._h, C.byref(h)), "hm_hss_to_hodlr")
+        return Matrix(h, "hodlr", self.tree)
+
     def reserve(self, r_max):
         check(lib.hm_matrix_reserve(self._h, int(r_max)), "hm_matrix_reserve")
 
