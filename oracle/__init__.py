@@ -25,6 +25,8 @@ define, so the oracle is that definition written out in float64:
                   (A^T)(I, J) = A(J, I)^T and the product Y = A^T X.
 * ``convert``  -- hss2hodlr (Sec. 3.5): HODLR generators of an HSS matrix from
                   its explicit nested bases.
+* ``hadamard`` -- generators of A o B (Sec. 4.5, Eq. 4.1, Fig. 4.3): transpose
+                  Khatri-Rao factors, Kronecker couplings and translations.
 * ``fig41``    -- the recursive HODLR product and the four-step HSS product of
                   Fig. 4.1, kept only to show which reading of the printed
                   coupling loop agrees with the definition.
@@ -33,4 +35,4 @@ Every function is pinned by ``tests/test_oracle_*.py`` against brute force,
 closed forms and exact-rank fixtures; none is "parity unpinned".
 """
 
-from . import tree, dense, matmat, expkernel, bounds, fig41, transpose, convert  # noqa: F401
+from . import tree, dense, matmat, expkernel, bounds, fig41, transpose, convert, hadamard  # noqa: F401

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import bounds, convert as CV, dense, expkernel, fig41, matmat as M, transpose as TR, tree as T
+from oracle import bounds, convert as CV, dense, expkernel, fig41, hadamard as HD, matmat as M, transpose as TR, tree as T
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -592,4 +592,74 @@ def test_hss_to_hodlr_planted_mistakes(monkeypatch, plant):
         return h
     monkeypatch.setattr(CV, "hss_to_hodlr", bad)
     got = brute_dense(c, CV.hss_to_hodlr(c, g))
+    assert not np.allclose(got, ref, rtol=1e-6, atol=1e-6), plant
+
+
+# --------------------------------------------------------------------------
+# Hadamard product (Sec. 4.5, Eq. 4.1, Fig. 4.3)
+# --------------------------------------------------------------------------
+
+def test_khatri_rao_t_definition():
+    C_ = np.arange(6.0).reshape(3, 2)
+    D_ = np.arange(9.0).reshape(3, 3) + 1
+    KR = HD.khatri_rao_t(C_, D_)
+    for i in range(3):
+        for a1 in range(2):
+            for a2 in range(3):
+                assert KR[i, a1 * 3 + a2] == C_[i, a1] * D_[i, a2]
+
+
+@pytest.mark.parametrize("kind", ["hodlr", "hss"])
+@pytest.mark.parametrize("name,c", SMALL_TREES + [("variable_p3", T.default_leaf_ends(40, 5))])
+def test_hadamard_brute_force(kind, name, c):
+    """Every entry of the Hadamard generators, evaluated on its own, is the
+    product of the entries of A and B (ranks differ per node and between A and B)."""
+    gA = _mixed_gens(kind, c, 51)
+    rng = np.random.default_rng(52)
+    if kind == "hodlr":
+        gB = W.random_hodlr(rng, c, lambda q: (1 + (q * 5) % 2, 1 + q % 2))
+    else:
+        gB = W.random_hss(rng, c, lambda q: (1 + (q * 5) % 2, 2 + q % 2), orthonormal=False)
+    gC = HD.hadamard_gens(c, gA, gB)
+    assert np.allclose(brute_dense(c, gC), brute_dense(c, gA) * brute_dense(c, gB), rtol=1e-12, atol=1e-12), name
+
+
+def test_hadamard_with_ones_is_identity_map():
+    """A o ones = A, with the all-ones matrix in its exact rank-1 form."""
+    c = T.default_leaf_ends(37, 4)
+    for kind in ("hodlr", "hss"):
+        gA = _gens(kind, c, 55)
+        gO = W.ones_hodlr(c) if kind == "hodlr" else W.ones_hss(c)
+        X = np.random.default_rng(2).standard_normal((37, 3))
+        assert np.allclose(M.matmat(c, HD.hadamard_gens(c, gA, gO), X), M.matmat(c, gA, X), rtol=1e-12, atol=1e-12)
+
+
+def test_hadamard_rejects_mixed_kinds():
+    c = T.default_leaf_ends(20, 5)
+    with pytest.raises(ValueError):
+        HD.hadamard_gens(c, _gens("hodlr", c, 1), _gens("hss", c, 2))
+
+
+@pytest.mark.parametrize("plant", ["kron_of_stacked_r", "swapped_kr_order", "b12_from_b21"])
+def test_hadamard_planted_mistakes(monkeypatch, plant):
+    c = [6, 12, 18, 24, 30, 36, 42, 48]
+    rng = np.random.default_rng(57)
+    gA = W.random_hss(rng, c, 2, orthonormal=False)
+    gB = W.random_hss(rng, c, 3, orthonormal=False)
+    ref = brute_dense(c, gA) * brute_dense(c, gB)
+    orig = HD.hadamard_gens
+
+    def bad(c_, a_, b_):
+        gC = orig(c_, a_, b_)
+        for q in range(1, len(c_) - 1):
+            if plant == "kron_of_stacked_r":
+                K = np.kron(a_["RU"][q], b_["RU"][q])
+                gC["RU"][q] = K[:gC["RU"][q].shape[0]]
+        if plant == "swapped_kr_order":
+            gC["U"] = [HD.khatri_rao_t(b, a) for a, b in zip(a_["U"], b_["U"])]
+        if plant == "b12_from_b21":
+            gC["B12"] = [np.kron(a, b) for a, b in zip(a_["B21"], b_["B21"])]
+        return gC
+    monkeypatch.setattr(HD, "hadamard_gens", bad)
+    got = brute_dense(c, HD.hadamard_gens(c, gA, gB))
     assert not np.allclose(got, ref, rtol=1e-6, atol=1e-6), plant
