@@ -214,19 +214,25 @@ def tree_flops(c):
 
 
 def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases, clock_index=None,
-                 prof_steps=None, world=1, form=None):
+                 prof_steps=None, world=1, form=None, g_b=None):
     """Device throughput of one storage type (timed region without profiling
     events, so consecutive kernels overlap), then a profiled pass that brackets
     every kernel with CUDA events for per-kernel durations.  form="transpose"
     times Y = A^T X (matrices from hm_matrix_transpose); form="hodlr" times
-    the HODLR form of the HSS matrix (hm_hss_to_hodlr)."""
+    the HODLR form of the HSS matrix (hm_hss_to_hodlr); form="hadamard"
+    times the Hadamard product of g and g_b (hm_hadamard)."""
     td = torch.float64 if storage == "f64" else torch.float32
     xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
     dev = torch.device("cuda", torch.cuda.current_device())
     mats = []
     for _ in range(copies):
         A0 = hm.Matrix.create(tree, g, storage)
-        mats.append(A0.transpose() if form == "transpose" else A0.to_hodlr() if form == "hodlr" else A0)
+        if form == "hadamard":
+            B0 = hm.Matrix.create(tree, g_b, storage)
+            mats.append(A0.hadamard(B0))
+            del B0
+        else:
+            mats.append(A0.transpose() if form == "transpose" else A0.to_hodlr() if form == "hodlr" else A0)
         del A0
     Xh = torch.from_numpy(g["_X"].T.copy())
     Xs = [Xh.to(dev).to(xd).t() for _ in range(copies)]
@@ -704,7 +710,29 @@ def main():
                                           "dominant_kernel": PHASES[d],
                                           "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] /
                                                                 r_["phases"]["steps"] for k in range(4)}}
+            # the Hadamard product of two HSS matrices of ranks 8 and 4 (rank 32), same tree and X
+            import workloads as W
+            rng_h = W.rng_for(2, salt=11)
+            gA8 = W.random_hss(rng_h, c, 8)
+            gB4 = W.random_hss(rng_h, c, 4)
+            gA8["_X"] = X
+            r_, yhd = time_variant(hm, torch, tree, gA8, prec, st, 3, copies, True, prof_steps=min(st, 20),
+                                   form="hadamard", g_b=gB4)
+            d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
+            variants["hadamard"] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
+                                    "storage": prec, "ranks": "8 o 4 = 32", "generator_bytes": r_["generator_bytes"],
+                                    "dominant_kernel": PHASES[d],
+                                    "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] /
+                                                          r_["phases"]["steps"] for k in range(4)}}
         if not args.no_cpu and world == 1:
+            if "hadamard" in variants:
+                from oracle import hadamard as OHD
+                from oracle import matmat as OMM
+                hrows = sorted(set([0, N_ - 1] + list(range(255, N_, N_ // 190))))[:192]
+                Yh_o = OMM.matmat_rows(c, OHD.hadamard_gens(c, gA8, gB4), X, hrows)
+                variants["hadamard"]["err_vs_oracle"] = float(np.max(
+                    np.linalg.norm(yhd[hrows] - Yh_o, axis=0) / np.linalg.norm(Yh_o, axis=0)))
+                variants["hadamard"]["err_rows"] = len(hrows)
             if "transpose" in variants:
                 from oracle import transpose as OTR
                 trows = sorted(set([0, N_ - 1] + list(range(255, N_, N_ // 190))))[:192]

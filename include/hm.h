@@ -203,6 +203,28 @@ hm_status hm_matrix_transpose(const hm_matrix* A, hm_matrix** out);
  * on any error. */
 hm_status hm_hss_to_hodlr(const hm_matrix* S, hm_matrix** out);
 
+/* The Hadamard (entrywise) product C = A o B of two HODLR or two HSS
+ * matrices on the same cluster tree, as a new matrix on the current device
+ * (Sec. 4.5, Eq. 4.1, Fig. 4.3): D_C = D_A o D_B; every factor of C is the
+ * transpose Khatri-Rao product of A's and B's (row i = kron(row i of A's
+ * factor, row i of B's), column a1 * k_B + a2); HSS couplings
+ * B12_C = B12_A (x) B12_B, B21_C likewise, and each child's block of the
+ * stacked translation operators R_U = [R_l; R_r], R_V = [W_l; W_r] is the
+ * Kronecker product of A's and B's blocks for that child.  Ranks multiply
+ * (HODLR: per level; the padded ranks as stored); no recompression.
+ * Products are formed in the translation operators' type (float64 for HM_F64
+ * storage, float32 otherwise) and each stored entry of D and of the factors
+ * is rounded once to the storage type.
+ * Ownership: *out is a new handle owned by the caller (hm_destroy); A and B
+ * are not modified (they may be the same matrix).  Synchronous (legacy
+ * default stream).
+ * Errors: HM_EINVAL for a NULL out, handles that are not matrices, different
+ * kinds, storage types or cluster trees, or a current device other than
+ * theirs; HM_EUNSUPPORTED when a rank of C exceeds 4096; HM_ENOMEM /
+ * HM_ECUDA for allocation and other CUDA failures.  *out is NULL on any
+ * error. */
+hm_status hm_hadamard(const hm_matrix* A, const hm_matrix* B, hm_matrix** out);
+
 /* Reserves device scratch for products with up to r_max right-hand sides so
  * that later calls allocate nothing (needed before CUDA-graph capture).
  * Synchronous. */

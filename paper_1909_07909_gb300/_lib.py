@@ -83,6 +83,7 @@ _decl("hm_matrix_info", C.c_int, vp, C.POINTER(hm_matrix_info_t))
 _decl("hm_matrix_bytes", C.c_int, vp, C.POINTER(C.c_size_t))
 _decl("hm_matrix_transpose", C.c_int, vp, C.POINTER(vp))
 _decl("hm_hss_to_hodlr", C.c_int, vp, C.POINTER(vp))
+_decl("hm_hadamard", C.c_int, vp, vp, C.POINTER(vp))
 _decl("hm_matrix_reserve", C.c_int, vp, C.c_int64)
 _decl("hm_matrix_set_path", C.c_int, vp, C.c_int32)
 _decl("hm_matrix_set_tree", C.c_int, vp, C.c_int32)

@@ -170,6 +170,13 @@ class Matrix:
         check(lib.hm_hss_to_hodlr(self._h, C.byref(h)), "hm_hss_to_hodlr")
         return Matrix(h, "hodlr", self.tree)
 
+    def hadamard(self, other):
+        """The entrywise product of this matrix and ``other`` (same kind, tree
+        and storage) as a new matrix; ranks multiply."""
+        h = vp()
+        check(lib.hm_hadamard(self._h, other._h, C.byref(h)), "hm_hadamard")
+        return Matrix(h, self.kind, self.tree)
+
     def reserve(self, r_max):
         check(lib.hm_matrix_reserve(self._h, int(r_max)), "hm_matrix_reserve")
 

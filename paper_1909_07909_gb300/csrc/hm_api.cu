@@ -472,6 +472,8 @@ extern "C" hm_status hm_hss_create(const hm_tree* t, const hm_hss_gens* g, hm_dt
   const int Ke = round_up(ku_max, 8), Kp = round_up(kv_max, 8);
   A->Ke = Ke;
   A->Kp = Kp;
+  A->ku_max = ku_max;
+  A->kv_max = kv_max;
   A->We = A->m_pad + Ke;
   const int64_t n = t->n;
   Plane Ap, Wp;

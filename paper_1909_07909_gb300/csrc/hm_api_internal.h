@@ -50,6 +50,7 @@ struct hm_matrix {
   int p = 0, L = 1;
   std::vector<int64_t> ends;
   int m_max = 0, m_pad = 16, Ke = 0, Kp = 0, We = 16;
+  int ku_max = 0, kv_max = 0;   // HSS: largest row / column rank before padding (Ke, Kp: padded to 8)
   int kk[hmi::kMaxDepth + 2] = {0};
   int koff[hmi::kMaxDepth + 2] = {0};
   int64_t gen_elems = 0;

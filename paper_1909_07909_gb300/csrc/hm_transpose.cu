@@ -143,6 +143,8 @@ extern "C" hm_status hm_matrix_transpose(const hm_matrix* A, hm_matrix** out) {
   T->m_pad = A->m_pad;
   T->Ke = A->Kp;
   T->Kp = A->Ke;
+  T->ku_max = A->kv_max;
+  T->kv_max = A->ku_max;
   T->We = A->m_pad + T->Ke;
   for (int l = 0; l <= kMaxDepth + 1; ++l) {
     T->kk[l] = A->kk[l];
