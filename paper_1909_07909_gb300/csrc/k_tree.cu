@@ -17,8 +17,9 @@
 // cp.async.bulk copies in the order the CTA uses them (the first NS before
 // griddepcontrol.wait, overlapping the previous kernel).  The small products
 // run as warp tasks: a warp computes 32 output rows of one operator for all
-// RC columns (lane i holds row i; operator rows are conflict-free shared
-// loads, vector rows broadcasts).  A warp waits on the mbarrier of its own
+// RC columns (each lane a register tile of up to 4 rows by 2 columns, so a
+// step reads one 16-byte operator segment and one vector pair per lane).
+// A warp waits on the mbarrier of its own
 // slot; the warp that finishes the last task of a slot refills it, so the
 // ring runs ahead across level boundaries.  Every sum runs in the same order
 // as in the level kernels (fma over j from zero, then + y_c; paired FMAs
