@@ -27,6 +27,8 @@ define, so the oracle is that definition written out in float64:
                   its explicit nested bases.
 * ``hadamard`` -- generators of A o B (Sec. 4.5, Eq. 4.1, Fig. 4.3): transpose
                   Khatri-Rao factors, Kronecker couplings and translations.
+* ``solve``    -- Y = A^{-1} B by a dense LU solve of the defining matrix
+                  (Sec. 4.3), and the backward error of a candidate solution.
 * ``fig41``    -- the recursive HODLR product and the four-step HSS product of
                   Fig. 4.1, kept only to show which reading of the printed
                   coupling loop agrees with the definition.
@@ -35,4 +37,4 @@ Every function is pinned by ``tests/test_oracle_*.py`` against brute force,
 closed forms and exact-rank fixtures; none is "parity unpinned".
 """
 
-from . import tree, dense, matmat, expkernel, bounds, fig41, transpose, convert, hadamard  # noqa: F401
+from . import tree, dense, matmat, expkernel, bounds, fig41, transpose, convert, hadamard, solve  # noqa: F401

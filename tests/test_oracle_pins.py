@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import bounds, convert as CV, dense, expkernel, fig41, hadamard as HD, matmat as M, transpose as TR, tree as T
+from oracle import bounds, convert as CV, dense, expkernel, fig41, hadamard as HD, matmat as M, solve as SV, transpose as TR, tree as T
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -663,3 +663,54 @@ def test_hadamard_planted_mistakes(monkeypatch, plant):
     monkeypatch.setattr(HD, "hadamard_gens", bad)
     got = brute_dense(c, HD.hadamard_gens(c, gA, gB))
     assert not np.allclose(got, ref, rtol=1e-6, atol=1e-6), plant
+
+
+# --------------------------------------------------------------------------
+# Y = A^{-1} B (Sec. 4.3, `A\\v` of Table 4.2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["hodlr", "hss"])
+@pytest.mark.parametrize("name,c", [t for t in SMALL_TREES if int(t[1][-1]) > 0])
+def test_solve_against_brute_force(kind, name, c):
+    """The independently evaluated dense A times the oracle's solution gives B."""
+    g = _gens(kind, c, 61)
+    n = int(c[-1])
+    B = np.random.default_rng(3).standard_normal((n, 3))
+    Y = SV.solve_dense(c, g, B)
+    Ab = brute_dense(c, g)
+    assert np.allclose(Ab @ Y, B, rtol=1e-10, atol=1e-10), name
+
+
+@pytest.mark.parametrize("fmt", ["hodlr", "hss"])
+def test_solve_closed_form_tridiag_inverse(fmt):
+    """A = T^{-1} for T = tridiag(-1, 2, -1): A^{-1} b = T b."""
+    n = 77
+    c = T.default_leaf_ends(n, 9)
+    g = W.tridiag_inverse_hodlr(c) if fmt == "hodlr" else W.tridiag_inverse_hss(c)
+    b = np.random.default_rng(2).standard_normal((n, 2))
+    Y = SV.solve_dense(c, g, b)
+    assert np.allclose(Y, _tridiag(n) @ b, rtol=1e-9, atol=1e-9)
+
+
+def test_solve_frobenius_and_residual():
+    c = T.default_leaf_ends(60, 8)
+    for kind in ("hodlr", "hss"):
+        g = _mixed_gens(kind, c, 63)
+        Ab = brute_dense(c, g)
+        assert np.isclose(SV.frobenius(c, g), np.linalg.norm(Ab), rtol=1e-13)
+        B = np.random.default_rng(4).standard_normal((60, 2))
+        Y = SV.solve_dense(c, g, B)
+        assert SV.residual(c, g, Y, B) <= 1e-14
+        assert SV.residual(c, g, Y + 1e-3, B) > 1e-6
+        assert np.isclose(SV.residual(c, g, np.zeros_like(B), B), 1.0)
+
+
+def test_solve_planted_mistake_transposed_matrix(monkeypatch):
+    """Solving with A^T instead of A fails the brute-force pin (A is not symmetric)."""
+    c = [6, 12, 18, 24, 30, 36, 42, 48]
+    g = _gens("hss", c, 65, k=3)
+    B = np.random.default_rng(5).standard_normal((48, 2))
+    orig = dense.dense
+    monkeypatch.setattr(dense, "dense", lambda c_, g_: orig(c_, g_).T)
+    Y = SV.solve_dense(c, g, B)
+    assert not np.allclose(brute_dense(c, g) @ Y, B, rtol=1e-6, atol=1e-6)
