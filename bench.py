@@ -164,7 +164,7 @@ class ClockSampler:
 
 def make_inputs():
     import workloads as W
-    rng = W.rng_for(2)
+    rng = W.rng_named("hss_n65536_m256_k32_r64")
     import paper_1909_07909_gb300 as hm
     tree = hm.Tree.default(N_, LEAF)
     c = tree.leaf_ends
@@ -377,7 +377,7 @@ def run_reference(args):
     import numpy as np
     import workloads as W
     from oracle import tree as OT
-    rng = W.rng_for(2)
+    rng = W.rng_named("hss_n65536_m256_k32_r64")
     c = OT.default_leaf_ends(N_, LEAF)
     g = W.random_hss(rng, c, RANK)
     X = rng.standard_normal((N_, RHS))
@@ -417,7 +417,7 @@ def run_batched(args):
     import workloads as W
     import paper_1909_07909_gb300 as hm
     torch.cuda.set_device(0)
-    rng = W.rng_for(4)
+    rng = W.rng_named("batched_512")
     count = args.count or 512
     spec = W.batch_spec(rng, count=count)
     out = {"metric": METRIC, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -505,7 +505,7 @@ def run_serve(args):
     import workloads as W
     import paper_1909_07909_gb300 as hm
     torch.cuda.set_device(0)
-    rng = W.rng_for(5)
+    rng = W.rng_named("serving_64_hss")
     count = args.count or 64
     spec = W.serve_spec(rng, count=count)
     server = hm.Server(100 << 30, 4096)
@@ -561,7 +561,7 @@ def run_serve(args):
     f64 = []
     for j in range(min(count, 8)):
         tree = mats[j].tree
-        g = W.random_hss(W.rng_for(5, 100 + j), tree.leaf_ends, spec[j]["k"])
+        g = W.random_hss(W.rng_named("serving_64_hss", 100 + j), tree.leaf_ends, spec[j]["k"])
         A64 = hm.Matrix.create(tree, g, "f64")
         X = torch.randn((8, spec[j]["n"]), dtype=torch.float64, device="cuda").t()
         A64.matmat(X)
@@ -712,7 +712,7 @@ def main():
                                                                 r_["phases"]["steps"] for k in range(4)}}
             # the Hadamard product of two HSS matrices of ranks 8 and 4 (rank 32), same tree and X
             import workloads as W
-            rng_h = W.rng_for(2, salt=11)
+            rng_h = W.rng_named("hss_n65536_m256_k32_r64", salt=11)
             gA8 = W.random_hss(rng_h, c, 8)
             gB4 = W.random_hss(rng_h, c, 4)
             gA8["_X"] = X

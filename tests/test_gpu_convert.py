@@ -112,8 +112,8 @@ def test_converted_structure():
 
 def test_converted_full_size_sampled_rows():
     """HSS n = 65536, leaf 256, rank 32, r = 64, BF16: converted product on sampled rows."""
-    cfg = W.CONFIGS[2]
-    rng = W.rng_for(2)
+    cfg = W.workload("hss_n65536_m256_k32_r64")
+    rng = W.rng_named("hss_n65536_m256_k32_r64")
     c = OT.default_leaf_ends(cfg["n"], cfg["m"])
     g = W.random_hss(rng, c, cfg["k"])
     X = rng.standard_normal((cfg["n"], cfg["r"]))

@@ -136,8 +136,8 @@ def test_hadamard_with_ones_is_a(kind):
 
 def test_hadamard_full_size_sampled_rows():
     """HSS n = 65536, leaf 256: rank 8 o rank 4 = rank 32, BF16, r = 64."""
-    cfg = W.CONFIGS[2]
-    rng = W.rng_for(2, salt=9)
+    cfg = W.workload("hss_n65536_m256_k32_r64")
+    rng = W.rng_named("hss_n65536_m256_k32_r64", salt=9)
     c = OT.default_leaf_ends(cfg["n"], cfg["m"])
     gA = W.random_hss(rng, c, 8)
     gB = W.random_hss(rng, c, 4)

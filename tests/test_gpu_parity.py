@@ -214,8 +214,8 @@ def test_deterministic(kind, storage):
 
 def test_config_hodlr_n4096_f64_dense_oracle():
     """HODLR n=4096, leaf 128 (p=5), rank 8, r=1, FP64: full-vector dense oracle."""
-    cfg = W.CONFIGS[1]
-    rng = W.rng_for(1)
+    cfg = W.workload("hodlr_n4096_m128_k8_r1_f64")
+    rng = W.rng_named("hodlr_n4096_m128_k8_r1_f64")
     c = OT.default_leaf_ends(cfg["n"], cfg["m"])
     g = W.random_hodlr(rng, c, cfg["k"])
     X = rng.standard_normal((cfg["n"], 1))
@@ -241,8 +241,8 @@ def _sample_rows(c, count, seed):
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "bf16x2"])
 def test_config_hss_n65536_sampled_rows(storage):
     """HSS n=65536, leaf 256, rank 32, r=64 at full size; oracle on sampled rows."""
-    cfg = W.CONFIGS[2]
-    rng = W.rng_for(2)
+    cfg = W.workload("hss_n65536_m256_k32_r64")
+    rng = W.rng_named("hss_n65536_m256_k32_r64")
     c = OT.default_leaf_ends(cfg["n"], cfg["m"])
     g = W.random_hss(rng, c, cfg["k"])
     X = rng.standard_normal((cfg["n"], cfg["r"]))
@@ -262,7 +262,7 @@ def test_config_hss_n65536_sampled_rows(storage):
 @pytest.mark.parametrize("storage,r", [("f64", 1), ("f32", 1), ("bf16x2", 1), ("f32", 128), ("bf16x2", 128)])
 def test_config_exp_kernel_n262144(storage, r):
     """HODLR exp kernel n=262144, leaf 256, K=8: recurrence (r=1, all rows) or sampled rows."""
-    rng = W.rng_for(3)
+    rng = W.rng_named("hodlr_exp_n262144_m256_K8")
     n = 262144
     t = W.exp_points(rng, n)
     ck, lk = W.exp_params(8)

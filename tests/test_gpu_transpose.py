@@ -145,8 +145,8 @@ def test_transpose_swaps_row_and_column_ranks():
 
 def test_transpose_adjoint_identity_full_size():
     """<Z, A X> = <A^T Z, X> on the n = 65536, leaf 256, rank 32 HSS matrix (FP64)."""
-    cfg = W.CONFIGS[2]
-    rng = W.rng_for(2, salt=5)
+    cfg = W.workload("hss_n65536_m256_k32_r64")
+    rng = W.rng_named("hss_n65536_m256_k32_r64", salt=5)
     c = OT.default_leaf_ends(cfg["n"], cfg["m"])
     g = W.random_hss(rng, c, cfg["k"])
     A, At = _transposed(c, g, "f64")
@@ -162,8 +162,8 @@ def test_transpose_adjoint_identity_full_size():
 @pytest.mark.parametrize("storage", ["f64", "bf16"])
 def test_transpose_full_size_sampled_rows(storage):
     """A^T X for the HSS n = 65536, leaf 256, rank 32, r = 64 matrix; oracle on sampled rows."""
-    cfg = W.CONFIGS[2]
-    rng = W.rng_for(2)
+    cfg = W.workload("hss_n65536_m256_k32_r64")
+    rng = W.rng_named("hss_n65536_m256_k32_r64")
     c = OT.default_leaf_ends(cfg["n"], cfg["m"])
     g = W.random_hss(rng, c, cfg["k"])
     X = rng.standard_normal((cfg["n"], cfg["r"]))

@@ -17,7 +17,7 @@ __all__ = [
     "tridiag_inverse_hodlr", "tridiag_inverse_hss", "tridiag_hodlr",
     "ones_hodlr", "ones_hss", "diagonal_hodlr", "diagonal_hss",
     "lowrank_hodlr", "lowrank_hss", "zeros_like_gens",
-    "batch_spec", "serve_spec", "CONFIGS",
+    "batch_spec", "serve_spec", "CONFIGS", "workload", "rng_named",
 ]
 
 SEED_BASE = 1909_07909
@@ -475,3 +475,19 @@ def serve_spec(rng, count=64, log2n=(12, 18), ranks=(16, 32, 48, 64)):
     """Resident matrices of the serving workload: n = 2^e, e uniform; rank uniform."""
     return [dict(kind="hss", n=1 << int(rng.integers(log2n[0], log2n[1] + 1)),
                  k=int(rng.choice(ranks))) for _ in range(count)]
+
+
+def workload(name):
+    """The synthetic workload called `name` (its sizes and shapes)."""
+    for cfg in CONFIGS.values():
+        if cfg["name"] == name:
+            return cfg
+    raise KeyError(name)
+
+
+def rng_named(name, salt=0):
+    """The seeded stream of the workload called `name` (same seed as its id)."""
+    for key, cfg in CONFIGS.items():
+        if cfg["name"] == name:
+            return rng_for(key, salt)
+    raise KeyError(name)
