@@ -83,6 +83,25 @@ def test_invalid_handles_rejected():
     L.lib.hm_destroy(None)
 
 
+def test_derived_matrix_calls_reject_bad_handles_before_gpu_work():
+    """hm_matrix_transpose, hm_hss_to_hodlr and hm_hadamard check their
+    handles before any CUDA call."""
+    vp = C.c_void_p
+    junk = C.cast((C.c_uint32 * 8)(0xdeadbeef), vp)
+    t = hm.Tree.from_leaf_ends([4, 8])
+    out = vp()
+    for h in (None, junk, t._h):
+        assert L.lib.hm_matrix_transpose(h, C.byref(out)) == L.HM_EINVAL
+        assert out.value is None
+        assert L.lib.hm_hss_to_hodlr(h, C.byref(out)) == L.HM_EINVAL
+        assert out.value is None
+        assert L.lib.hm_hadamard(h, h, C.byref(out)) == L.HM_EINVAL
+        assert out.value is None
+    assert L.lib.hm_matrix_transpose(junk, None) == L.HM_EINVAL
+    assert L.lib.hm_hss_to_hodlr(junk, None) == L.HM_EINVAL
+    assert L.lib.hm_hadamard(junk, junk, None) == L.HM_EINVAL
+
+
 def test_create_rejects_bad_generators_before_gpu_work():
     t = hm.Tree.from_leaf_ends([4, 8])
     h = C.c_void_p()
