@@ -82,7 +82,26 @@ def build(force=False, verbose=False, jobs=None):
         if res.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
         os.replace(tmp, LIB)
+    _build_probe(exe)
     return LIB
+
+
+PROBE_SRC = os.path.join(HERE, "probe", "peak_probe.cu")
+PROBE_LIB = os.path.join(HERE, "libhm_probe.so")
+
+
+def _build_probe(exe):
+    """libhm_probe.so: the arithmetic-pipe peak probe (its own library; the
+    product path never calls it)."""
+    if os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [exe] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", PROBE_SRC, "-o", tmp]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s%s" % (PROBE_SRC, res.stdout, res.stderr))
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":
