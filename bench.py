@@ -5,13 +5,22 @@ Workload (one "step" = one product Y = A X through the C ABI):
   HSS, n = 65536, leaf 256 (p = 8), nested rank 32, 64 right-hand sides;
   leaf U, V orthonormal (Q of a Gaussian QR), translations R and couplings B
   iid N(0, 1/32) (variance), D ~ N(0,1) + 8 I, X ~ N(0,1); seeded.
-  Headline storage: --precision (default bf16) with float32 X and Y; the
-  other storages (f64, f32, bf16x2) are timed as variants in the same run.
+  Headline: FP64 storage, FP64 X and Y (the paper's arithmetic); the other
+  storages (BF16, split BF16, FP32) are timed as variants in the same run,
+  each with its time ratio to FP64 and its error against the FP64 oracle,
+  next to the HODLR n=4096 FP64 r=1 and exponential-kernel n=262144
+  (r = 1 and 128) workloads.
 
 Timing: W untimed steps, then exactly K steps bracketed by a barrier and
 torch.cuda.synchronize() on both sides, CUDA events on the launching stream,
 max over ranks.  The inputs rotate over several resident copies whose total
 exceeds the 135 MB L2, so every step streams its generators from HBM.
+
+Rooflines: the FP64 products are bound by the FP64 pipe (about 1/64 of the
+FP32 rate on this GPU), so their denominator is the FP64 FMA throughput that
+libhm_probe.so measures in this process; the FP32 tree kernel's is the FP32
+FMA throughput; the reduced-precision leaf kernels are HBM-bound and use the
+measured copy bandwidth of MEASURED_PEAKS.json.
 
 --impl reference times the CPU oracle (the FP64 dense-definition product)
 on a bounded sample of the same workload.  N > 1 (torchrun): each rank runs
@@ -19,6 +28,7 @@ its own replica (weak scaling, no collective on the data path).
 """
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -40,24 +50,33 @@ ESZ = {"f64": 8, "f32": 4, "bf16": 2, "bf16x2": 4}
 # bytes, TMA-loaded); split BF16 needs the float X for its lo part.
 X_DTYPE = {"f64": "f64", "f32": "f32", "bf16": "bf16", "bf16x2": "f32"}
 XSZ = {"f64": 8, "f32": 4, "bf16": 2}
+L2_BYTES = 135.5e6
+# FP64 FMA rate from the recipe's unit counts: 152 SMs x 2 FMA/cycle x 2 flops
+# x 2.07 GHz (NVIDIA's stated 1.25 TFLOP/s), and the FP32 SIMT rate: 152 SMs x
+# 128 lanes x 2 flops x 2.07 GHz.  Context for the measured denominators.
+FP64_NOMINAL_TFLOPS = 1.25
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hm", choices=["hm", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "f32", "f64", "bf16x2"])
+    ap.add_argument("--precision", default="f64", choices=["bf16", "f32", "f64", "bf16x2"])
     ap.add_argument("--copies", type=int, default=0, help="resident copies (0 = enough to exceed L2)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the n=4096 and n=262144 workloads")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-leaves", type=int, default=6, help="leaf row blocks in the CPU sample")
+    ap.add_argument("--cpu-leaves", type=int, default=6, help="leaf row blocks in the CPU oracle sample")
     ap.add_argument("--workload", default="hss", choices=["hss", "batched", "serve"],
                     help="hss: the HSS n=65536 headline; batched: 512 uneven matrices; serve: Poisson requests")
     ap.add_argument("--count", type=int, default=0, help="matrices in the batched / serving workload")
     ap.add_argument("--rates", default="1000,5000,10000,20000,50000")
     ap.add_argument("--seconds", type=float, default=1.0, help="arrival window per rate (serve)")
+    ap.add_argument("--probe-sweep", action="store_true",
+                    help="only print the FP32 / FP64 / FP64-mma pipe throughput over several launch shapes")
     return ap.parse_args()
 
 
@@ -102,9 +121,362 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP64 / FP32 FMA peaks of this GPU model (FMA-throughput probe, profiles/fma_peaks_probe.txt).
-FP64_TFLOPS = 1.199
-FP32_TFLOPS = 74.9
+PROBE_SHAPE = {"fp32": (0, 2, 256, 20000), "fp64": (1, 2, 256, 400)}
+
+
+def _probe_lib():
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_1909_07909_gb300", "libhm_probe.so"))
+    lib.hm_probe_peak.argtypes = [ctypes.c_int] * 5 + [ctypes.POINTER(ctypes.c_double),
+                                                       ctypes.POINTER(ctypes.c_double),
+                                                       ctypes.POINTER(ctypes.c_int)]
+    return lib
+
+
+def probe_sweep():
+    """Pipe throughput over launch shapes (FP32 FMA, FP64 FMA, FP64 mma.sync)."""
+    import torch
+    torch.cuda.set_device(0)
+    lib = _probe_lib()
+    rows = []
+    for which, name, iters in ((0, "fp32_fma", 20000), (1, "fp64_fma", 400), (2, "fp64_mma", 400)):
+        for bps, thr in ((1, 128), (1, 256), (2, 256), (4, 256), (8, 256)):
+            tf, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+            rc = lib.hm_probe_peak(which, bps, thr, iters, 3, ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(sms))
+            rows.append({"probe": name, "blocks_per_sm": bps, "threads": thr, "rc": rc, "tflops": tf.value,
+                         "ms": ms.value, "sms": sms.value})
+    print(json.dumps({"pipe_probe_sweep": rows}))
+    return 0
+
+
+def probe_pipes():
+    """FP32 and FP64 FMA throughput of this GPU, measured now by libhm_probe.so
+    (paper_1909_07909_gb300/probe/peak_probe.cu): SMs x 2 blocks x 256
+    threads, 8 independent FMA chains per thread, best of 3 launches after a
+    warm-up launch.  Returns {name: {"tflops", "ms", "shape"}}."""
+    lib = _probe_lib()
+    out = {}
+    for name, (which, bps, thr, iters) in PROBE_SHAPE.items():
+        tf, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        rc = lib.hm_probe_peak(which, bps, thr, iters, 3, ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(sms))
+        if rc != 0:
+            raise RuntimeError("pipe probe %s failed with CUDA error %d" % (name, rc))
+        out[name] = {"tflops": tf.value, "ms": ms.value,
+                     "shape": "%d SMs x %d blocks x %d threads, 8 FMA chains per thread, %d x 4 FMAs per "
+                              "chain, best of 3" % (sms.value, bps, thr, iters)}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work of one product, per phase (the roofline's numerators)
+# ---------------------------------------------------------------------------
+
+def _elems(blocks):
+    import numpy as np
+    return int(sum(np.asarray(b).size for b in blocks if b is not None))
+
+
+def gen_counts(g):
+    """Generator element counts of a workload's generator dict (unpadded)."""
+    if g["kind"] == "hodlr":
+        return {"D": _elems(g["D"]), "U": _elems(g["U12"]) + _elems(g["U21"]),
+                "V": _elems(g["V12"]) + _elems(g["V21"]), "tree": 0}
+    return {"D": _elems(g["D"]), "U": _elems(g["U"]), "V": _elems(g["V"]),
+            "tree": _elems(g["RU"]) + _elems(g["RV"]) + _elems(g["B12"]) + _elems(g["B21"])}
+
+
+def phase_work(g, n, r, storage):
+    """Algorithmic bytes and flops per launch of every phase of one product
+    (generators read once in the storage type, X read, Y written; per-node
+    k x r intermediates excluded).  The tree operators are held in FP64 for
+    FP64 storage and in FP32 otherwise.  Phase names follow
+    hm_matrix_phase_times: project, tree, tree_down, expand, dpart (the FP64
+    diagonal-block product D X; the expansion then adds E Z to Y)."""
+    gc = gen_counts(g)
+    s = ESZ[storage]
+    xs = XSZ[X_DTYPE[storage]]
+    ys = 8 if storage == "f64" else 4
+    ts = 8 if storage == "f64" else 4
+    io = n * r
+    w = {"project": {"bytes": gc["V"] * s + io * xs, "flops": 2 * gc["V"] * r},
+         "tree": {"bytes": gc["tree"] * ts, "flops": 2 * gc["tree"] * r},
+         "tree_down": {"bytes": 0, "flops": 0},
+         "expand": {"bytes": (gc["D"] + gc["U"]) * s + io * (xs + ys), "flops": 2 * (gc["D"] + gc["U"]) * r},
+         "dpart": {"bytes": 0, "flops": 0}}
+    return w, gc
+
+
+def split_work(w, gc, n, r, storage):
+    """The FP64 wide-block path runs D X as its own launch (phase dpart) and
+    the expansion as Y += E Z (reading and writing Y)."""
+    s, xs, ys = ESZ[storage], XSZ[X_DTYPE[storage]], 8
+    w = dict(w)
+    w["dpart"] = {"bytes": gc["D"] * s + n * r * (xs + ys), "flops": 2 * gc["D"] * r}
+    w["expand"] = {"bytes": gc["U"] * s + n * r * 2 * ys, "flops": 2 * gc["U"] * r}
+    return w
+
+
+PHASES = ["project", "tree", "tree_down", "expand", "dpart"]
+KERNEL_NAMES = {
+    ("f64", "dpart"): "k_leaf_f64<1, 32> (FP64 diagonal-block product D X, register-tiled)",
+    ("f64", "expand"): "k_leaf_f64<2, *> / k_expand<F64> (FP64 leaf expansion)",
+    ("f64", "project"): "k_leaf_f64<0, *> / k_project<F64> (FP64 leaf projection)",
+    ("f64", "tree"): "k_tree_cluster<double, *> (FP64 tree)",
+}
+
+
+def roofline(w, phases, storage, peaks, pipes, tc):
+    """Roofline of the dominant kernel of one product from the profiled
+    pass's per-launch CUDA-event durations.  FP64: every phase is bound by
+    the FP64 pipe.  Otherwise the bound is the one the kernel's arithmetic
+    intensity puts it under: FP32 FMA pipe (SIMT and the FP32 tree), BF16
+    tensor pipe (tensor-core leaf kernels, `tc`), or HBM."""
+    ms, ln = phases["ms"], phases["launches"]
+    dom = max(range(len(PHASES)), key=lambda k: ms[k])
+    name = PHASES[dom]
+    avg_ms = ms[dom] / max(ln[dom], 1)
+    wk = w[name]
+    hbm = peaks["hbm_gbs"]
+    if storage == "f64":
+        bound, peak, unit, ach = "alu", pipes["fp64"]["tflops"], "TFLOP/s", wk["flops"] / (avg_ms * 1e-3) / 1e12
+        src = "FP64 FMA throughput measured in this run (libhm_probe.so, %s)" % pipes["fp64"]["shape"]
+    else:
+        if name == "tree" or not tc:
+            pk_f = pipes["fp32"]["tflops"]
+            src_f = "FP32 FMA throughput measured in this run (libhm_probe.so, %s)" % pipes["fp32"]["shape"]
+        else:
+            pk_f = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
+            src_f = "BF16 dense tensor peak (MEASURED_PEAKS.json, sustained)"
+        intensity = wk["flops"] / max(wk["bytes"], 1)
+        if wk["bytes"] == 0 or intensity * hbm * 1e9 >= pk_f * 1e12:
+            bound, peak, unit, src = ("alu" if name == "tree" or not tc else "tensor"), pk_f, "TFLOP/s", src_f
+            ach = wk["flops"] / (avg_ms * 1e-3) / 1e12
+        else:
+            bound, peak, unit, src = "hbm", hbm, "GB/s", "copy bandwidth (MEASURED_PEAKS.json)"
+            ach = wk["bytes"] / (avg_ms * 1e-3) / 1e9
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "peak_source": src, "phase": name, "ms_per_launch": avg_ms,
+            "bytes_per_launch": wk["bytes"], "flops_per_launch": wk["flops"]}
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def make_inputs():
+    import workloads as W
+    rng = W.rng_named("hss_n65536_m256_k32_r64")
+    import paper_1909_07909_gb300 as hm
+    tree = hm.Tree.default(N_, LEAF)
+    c = tree.leaf_ends
+    g = W.random_hss(rng, c, RANK)
+    X = rng.standard_normal((N_, RHS))
+    return tree, c, g, X
+
+
+def fp64_step_bytes(c):
+    """Algorithmic bytes of one FP64 product: all generators read once, X read, Y written."""
+    L = len(c)
+    sizes = [c[0]] + [c[i] - c[i - 1] for i in range(1, L)]
+    elems = sum(m * m for m in sizes) + 2 * N_ * RANK + max(L - 2, 0) * 4 * RANK * RANK + \
+        max(2 * L - 2, 0) * RANK * RANK
+    return 8 * elems + N_ * RHS * 16
+
+
+def step_bytes(A, storage, n, r):
+    ys = 8 if storage == "f64" else 4
+    return A.generator_bytes() + n * r * (XSZ[X_DTYPE[storage]] + ys)
+
+
+def copies_for(bytes_per_step, want=0):
+    return want or max(1 if bytes_per_step > 1.5 * L2_BYTES else 2, math.ceil(2.2 * L2_BYTES / bytes_per_step))
+
+
+def time_variant(hm, torch, tree, g, storage, X, steps, warmup, copies, clock_index=None, prof_steps=None,
+                 world=1, form=None, g_b=None):
+    """Device throughput of one storage type on the product Y = A X (timed
+    region without profiling events, so consecutive kernels overlap), then a
+    profiled pass that brackets every kernel with CUDA events for per-kernel
+    durations.  form="transpose" times Y = A^T X (matrices from
+    hm_matrix_transpose); form="hodlr" the HODLR form of the HSS matrix
+    (hm_hss_to_hodlr); form="hadamard" the Hadamard product of g and g_b."""
+    n, r = X.shape
+    td = torch.float64 if storage == "f64" else torch.float32
+    xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mats = []
+    for _ in range(copies):
+        A0 = hm.Matrix.create(tree, g, storage)
+        if form == "hadamard":
+            B0 = hm.Matrix.create(tree, g_b, storage)
+            mats.append(A0.hadamard(B0))
+            del B0
+        else:
+            mats.append(A0.transpose() if form == "transpose" else A0.to_hodlr() if form == "hodlr" else A0)
+        del A0
+    Xh = torch.from_numpy(X.T.copy())
+    Xs = [Xh.to(dev).to(xd).t() for _ in range(copies)]
+    Ys = [torch.empty((r, n), dtype=td, device=dev).t() for _ in range(copies)]
+    for A in mats:
+        A.reserve(r)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    code = hm.HM_F64 if storage == "f64" else hm.HM_F32
+    xcode = {"f64": hm.HM_F64, "f32": hm.HM_F32, "bf16": hm.HM_BF16}[X_DTYPE[storage]]
+
+    def run(i):
+        j = i % copies
+        mats[j].matmat_raw(r, Xs[j].data_ptr(), n, xcode, Ys[j].data_ptr(), n, code, sptr)
+
+    for i in range(warmup):
+        run(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(clock_index) if clock_index is not None else None
+    if sampler:
+        sampler.__enter__()
+    torch.cuda.synchronize()
+    rank_barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        run(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rank_barrier(world)
+    if sampler:
+        sampler.__exit__()
+    ms_total = e0.elapsed_time(e1)
+    ps = prof_steps or steps
+    for A in mats:
+        A.profile(True)
+        A.phase_times()
+    for i in range(ps):
+        run(i)
+    torch.cuda.synchronize()
+    acc_ms = [0.0] * len(PHASES)
+    acc_n = [0] * len(PHASES)
+    for A in mats:
+        ms, nl = A.phase_times()
+        A.profile(False)
+        for k in range(len(PHASES)):
+            acc_ms[k] += ms[k]
+            acc_n[k] += nl[k]
+    info = mats[0].info()
+    res = {"ms_total": ms_total, "ms_per_step": ms_total / steps,
+           "bytes_per_step": step_bytes(mats[0], storage, n, r),
+           "phases": {"ms": acc_ms, "launches": acc_n, "steps": ps},
+           "clocks": sampler.summary() if sampler else None,
+           "generator_bytes": mats[0].generator_bytes(), "info": info,
+           "launches_per_step": sum(acc_n) / ps}
+    res["gbs"] = res["bytes_per_step"] / (res["ms_per_step"] * 1e-3) / 1e9
+    Y0 = Ys[0].to(torch.float64).cpu().numpy()
+    del mats
+    return res, Y0
+
+
+def e2e_host(hm, torch, tree, g, storage, X, steps, copies):
+    """The same product through the C ABI with pinned host buffers: every
+    call copies X to the device and Y back inside the timed region.  The
+    matrices rotate over the same number of resident copies as the device
+    arm, so every product streams its generators from HBM."""
+    n, r = X.shape
+    mats = [hm.Matrix.create(tree, g, storage) for _ in range(copies)]
+    for A in mats:
+        A.reserve(r)
+    f64 = storage == "f64"
+    td = torch.float64 if f64 else torch.float32
+    xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
+    Xp = torch.from_numpy(X.T.copy()).to(xd).pin_memory()
+    Yp = torch.empty((r, n), dtype=td).pin_memory()
+    code = hm.HM_F64 if f64 else hm.HM_F32
+    xcode = {"f64": hm.HM_F64, "f32": hm.HM_F32, "bf16": hm.HM_BF16}[X_DTYPE[storage]]
+    stream = torch.cuda.current_stream().cuda_stream
+    for i in range(max(3, copies)):
+        mats[i % copies].matmat_raw(r, Xp.data_ptr(), n, xcode, Yp.data_ptr(), n, code, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        mats[i % copies].matmat_raw(r, Xp.data_ptr(), n, xcode, Yp.data_ptr(), n, code, stream)
+    dt = (time.perf_counter() - t0) / steps
+    ys = 8 if f64 else 4
+    xs = XSZ[X_DTYPE[storage]]
+    b = mats[0].generator_bytes() + n * r * (xs + ys)
+    del mats
+    return {"value": b / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n * r * xs,
+            "d2h_bytes_per_step": n * r * ys, "ms_per_step": dt * 1e3,
+            "l2": "%d rotating resident matrices" % copies}
+
+
+def cpu_fast_baseline(c, g, X, runs=3):
+    """The paper's fast product (Fig. 4.1) in FP64 C++/OpenMP on all host
+    cores (cpu_baseline/libhm_cpu.so): one warm-up product, then the best of
+    `runs` full products.  Returns (seconds, threads, Y)."""
+    import cpu_baseline as CB
+    M = CB.CpuMatrix(c, g)
+    Y = M.matmat(X)
+    best = 1e30
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        M.matmat(X, out=Y)
+        best = min(best, time.perf_counter() - t0)
+    M.close()
+    return best, CB.threads(), Y
+
+
+def cpu_oracle_sample(c, g, X, leaves):
+    """Oracle (dense-definition product) on `leaves` leaf row blocks; returns
+    (seconds, rows, Yrows)."""
+    import numpy as np
+    from oracle import matmat as OM
+    from oracle import tree as OT
+    t0 = time.perf_counter()
+    blocks = OM.matmat_leaves(c, g, X, leaves)
+    dt = time.perf_counter() - t0
+    rows = []
+    for i in leaves:
+        a, b = OT.leaf_range(c, i)
+        rows.extend(range(a, b))
+    return dt, rows, np.vstack(blocks)
+
+
+def traffic_for(kernel_key):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json, if the kernel
+    source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    ent = rec.get(kernel_key)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for f in ent.get("sources", []):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != ent.get("sha256"):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def col_err(Y, ref):
+    import numpy as np
+    num = np.linalg.norm(Y - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    return float(np.max(num / np.where(den == 0, 1.0, den)))
+
+
+def summarize(res, w, storage, peaks, pipes, tc, extra=None):
+    ph = res["phases"]
+    roof = roofline(w, ph, storage, peaks, pipes, tc)
+    out = {"value": res["gbs"], "unit": "GB/s", "ms_per_step": res["ms_per_step"],
+           "bytes_per_step": res["bytes_per_step"],
+           "phase_ms_per_step": {PHASES[k]: ph["ms"][k] / ph["steps"] for k in range(len(PHASES))},
+           "roofline": roof}
+    if extra:
+        out.update(extra)
+    return out
 
 
 class ClockSampler:
@@ -160,214 +532,6 @@ class ClockSampler:
         loaded = [v for v in sm if v > 0.5 * (mx or max(sm))] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
-
-
-def make_inputs():
-    import workloads as W
-    rng = W.rng_named("hss_n65536_m256_k32_r64")
-    import paper_1909_07909_gb300 as hm
-    tree = hm.Tree.default(N_, LEAF)
-    c = tree.leaf_ends
-    g = W.random_hss(rng, c, RANK)
-    X = rng.standard_normal((N_, RHS))
-    return tree, c, g, X
-
-
-def step_bytes(A, storage, xs=4, ys=4):
-    return A.generator_bytes() + N_ * RHS * (xs + ys)
-
-
-# Phase slots of hm_matrix_phase_times: the leaf projection, the tree (the
-# cluster kernel runs upsweep, couplings and downsweep in this one slot; the
-# per-level kernels use it for the upsweep), the per-level downsweep, the
-# leaf expansion.
-PHASES = ["project", "tree", "tree_down", "expand"]
-
-
-def phase_bytes(storage, c):
-    """Algorithmic bytes per launch: the expansion reads D and U, X and writes
-    Y; the projection reads V and X; the tree kernels read their operators
-    once (R_V, B12, B21 upward; R_U downward; held in FP64 for FP64 storage,
-    else FP32).  Per-node k x r intermediates are excluded, as for the whole
-    step."""
-    s = ESZ[storage]
-    xs = XSZ[X_DTYPE[storage]]
-    ys = 8 if storage == "f64" else 4
-    ts = 8 if storage == "f64" else 4
-    L = len(c)
-    sizes = [c[0]] + [c[i] - c[i - 1] for i in range(1, L)]
-    d_elems = sum(m * m for m in sizes)
-    expand = (d_elems + N_ * RANK) * s + N_ * RHS * (xs + ys)
-    project = N_ * RANK * s + N_ * RHS * xs
-    internal = L - 1
-    tree = internal * (2 * RANK * RANK + 2 * RANK * RANK) * ts + internal * 2 * RANK * RANK * ts
-    return {"project": project, "tree": tree, "tree_down": 0, "expand": expand}
-
-
-def tree_flops(c):
-    """FLOPs of the HSS tree for the workload: R_V^T on every internal node
-    but the root, B12 and B21 on every internal node, one R_U half per node
-    of levels 2 .. p (2 flops per multiply-add, every right-hand side)."""
-    L = len(c)
-    k2 = RANK * RANK
-    return 2 * RHS * ((L - 2) * 2 * k2 + (L - 1) * 2 * k2 + (2 * L - 4) * k2)
-
-
-def time_variant(hm, torch, tree, g, storage, steps, warmup, copies, want_phases, clock_index=None,
-                 prof_steps=None, world=1, form=None, g_b=None):
-    """Device throughput of one storage type (timed region without profiling
-    events, so consecutive kernels overlap), then a profiled pass that brackets
-    every kernel with CUDA events for per-kernel durations.  form="transpose"
-    times Y = A^T X (matrices from hm_matrix_transpose); form="hodlr" times
-    the HODLR form of the HSS matrix (hm_hss_to_hodlr); form="hadamard"
-    times the Hadamard product of g and g_b (hm_hadamard)."""
-    td = torch.float64 if storage == "f64" else torch.float32
-    xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
-    dev = torch.device("cuda", torch.cuda.current_device())
-    mats = []
-    for _ in range(copies):
-        A0 = hm.Matrix.create(tree, g, storage)
-        if form == "hadamard":
-            B0 = hm.Matrix.create(tree, g_b, storage)
-            mats.append(A0.hadamard(B0))
-            del B0
-        else:
-            mats.append(A0.transpose() if form == "transpose" else A0.to_hodlr() if form == "hodlr" else A0)
-        del A0
-    Xh = torch.from_numpy(g["_X"].T.copy())
-    Xs = [Xh.to(dev).to(xd).t() for _ in range(copies)]
-    Ys = [torch.empty((RHS, N_), dtype=td, device=dev).t() for _ in range(copies)]
-    for A in mats:
-        A.reserve(RHS)
-    stream = torch.cuda.current_stream()
-    sptr = stream.cuda_stream
-    code = hm.HM_F64 if storage == "f64" else hm.HM_F32
-    xcode = {"f64": hm.HM_F64, "f32": hm.HM_F32, "bf16": hm.HM_BF16}[X_DTYPE[storage]]
-
-    def run(i):
-        j = i % copies
-        mats[j].matmat_raw(RHS, Xs[j].data_ptr(), N_, xcode, Ys[j].data_ptr(), N_, code, sptr)
-
-    for i in range(warmup):
-        run(i)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(clock_index) if clock_index is not None else None
-    if sampler:
-        sampler.__enter__()
-    torch.cuda.synchronize()
-    rank_barrier(world)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for i in range(steps):
-        run(i)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    rank_barrier(world)
-    if sampler:
-        sampler.__exit__()
-    ms_total = e0.elapsed_time(e1)
-    phases = None
-    if want_phases:
-        ps = prof_steps or steps
-        for A in mats:
-            A.profile(True)
-            A.phase_times()
-        for i in range(ps):
-            run(i)
-        torch.cuda.synchronize()
-        acc_ms = [0.0] * 4
-        acc_n = [0] * 4
-        for A in mats:
-            ms, n = A.phase_times()
-            A.profile(False)
-            for k in range(4):
-                acc_ms[k] += ms[k]
-                acc_n[k] += n[k]
-        phases = {"ms": acc_ms, "launches": acc_n, "steps": ps}
-    es = 8 if storage == "f64" else 4
-    res = {"ms_total": ms_total, "ms_per_step": ms_total / steps,
-           "bytes_per_step": step_bytes(mats[0], storage, XSZ[X_DTYPE[storage]], es),
-           "phases": phases, "clocks": sampler.summary() if sampler else None,
-           "generator_bytes": mats[0].generator_bytes()}
-    res["gbs"] = res["bytes_per_step"] / (res["ms_per_step"] * 1e-3) / 1e9
-    Y0 = Ys[0].to(torch.float64).cpu().numpy()
-    del mats
-    return res, Y0
-
-
-def e2e_host(hm, torch, tree, g, storage, steps):
-    """Same product through the C ABI with pinned host buffers (copies inside)."""
-    import numpy as np
-    A = hm.Matrix.create(tree, g, storage)
-    A.reserve(RHS)
-    f64 = storage == "f64"
-    td = torch.float64 if f64 else torch.float32
-    xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
-    Xp = torch.from_numpy(g["_X"].T.copy()).to(xd).pin_memory()
-    Yp = torch.empty((RHS, N_), dtype=td).pin_memory()
-    code = hm.HM_F64 if f64 else hm.HM_F32
-    xcode = {"f64": hm.HM_F64, "f32": hm.HM_F32, "bf16": hm.HM_BF16}[X_DTYPE[storage]]
-    stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(3):
-        A.matmat_raw(RHS, Xp.data_ptr(), N_, xcode, Yp.data_ptr(), N_, code, stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        A.matmat_raw(RHS, Xp.data_ptr(), N_, xcode, Yp.data_ptr(), N_, code, stream)
-    dt = (time.perf_counter() - t0) / steps
-    es = 8 if f64 else 4
-    xs = XSZ[X_DTYPE[storage]]
-    b = A.generator_bytes() + N_ * RHS * (xs + es)
-    del np
-    return {"value": b / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": N_ * RHS * xs,
-            "d2h_bytes_per_step": N_ * RHS * es, "ms_per_step": dt * 1e3}
-
-
-def fp64_step_bytes(c):
-    """Algorithmic bytes of one FP64 product: all generators read once, X read, Y written."""
-    L = len(c)
-    sizes = [c[0]] + [c[i] - c[i - 1] for i in range(1, L)]
-    elems = sum(m * m for m in sizes) + 2 * N_ * RANK + max(L - 2, 0) * 4 * RANK * RANK + \
-        max(2 * L - 2, 0) * RANK * RANK
-    return 8 * elems + N_ * RHS * 16
-
-
-def cpu_oracle_sample(c, g, X, leaves):
-    """Oracle (dense-definition product) on `leaves` leaf row blocks; returns
-    (seconds, rows, Yrows, cores)."""
-    import numpy as np
-    from oracle import matmat as OM
-    from oracle import tree as OT
-    t0 = time.perf_counter()
-    blocks = OM.matmat_leaves(c, g, X, leaves)
-    dt = time.perf_counter() - t0
-    rows = []
-    for i in leaves:
-        a, b = OT.leaf_range(c, i)
-        rows.extend(range(a, b))
-    return dt, rows, np.vstack(blocks)
-
-
-def traffic_for(kernel_key):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.json, if the kernel
-    source has not changed since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as fh:
-            rec = json.load(fh)
-    except Exception:
-        return None
-    ent = rec.get(kernel_key)
-    if not ent:
-        return None
-    h = hashlib.sha256()
-    for f in ent.get("sources", []):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest() != ent.get("sha256"):
-        return None
-    return ent.get("bytes_per_launch")
 
 
 def run_reference(args):
@@ -591,11 +755,77 @@ def run_serve(args):
     return 0
 
 
+def run_workloads(hm, torch, np, peaks, pipes, steps, warmup, with_cpu):
+    """The other single-matrix workloads, each with its own roofline:
+    HODLR n=4096 leaf 128 rank 8 r=1 FP64 (L2-resident: 48 rotating copies)
+    and the exact rank-8 exponential kernel HODLR n=262144 leaf 256 at r=1 and
+    r=128 in every storage; errors against the oracle (the O(nK) recurrence
+    for r=1, sampled dense rows for r=128, the dense product for n=4096)."""
+    import workloads as W
+    from oracle import expkernel as OE, matmat as OM
+    out = {}
+    # HODLR n=4096, FP64, r=1
+    rng = W.rng_named("hodlr_n4096_m128_k8_r1_f64")
+    tree = hm.Tree.default(4096, 128)
+    c = tree.leaf_ends
+    g = W.random_hodlr(rng, c, 8)
+    X = rng.standard_normal((4096, 1))
+    w, _ = phase_work(g, 4096, 1, "f64")
+    res, Y = time_variant(hm, torch, tree, g, "f64", X, max(steps, 200), warmup, 48, prof_steps=50)
+    ent = summarize(res, w, "f64", peaks, pipes, False,
+                    {"workload": "hodlr n=4096 leaf=128 rank=8 r=1", "storage": "f64",
+                     "l2": "48 rotating copies of %.1f MB (one matrix fits in L2)" % (res["bytes_per_step"] / 1e6),
+                     "launches_per_step": res["launches_per_step"]})
+    if with_cpu:
+        ent["err_vs_oracle"] = col_err(Y, OM.matmat(c, g, X))
+    out["hodlr_n4096_r1_f64"] = ent
+    # exponential kernel, n=262144
+    rng = W.rng_named("hodlr_exp_n262144_m256_K8")
+    n = 262144
+    t = W.exp_points(rng, n)
+    ck, lk = W.exp_params(8)
+    tree = hm.Tree.default(n, 256)
+    c = tree.leaf_ends
+    g = W.exp_kernel_hodlr(t, c, ck, lk)
+    rows = sorted(set([0, n - 1] + [int(v) for v in np.linspace(255, n - 2, 158)]))
+    for r, storages in ((1, ("f32", "bf16", "bf16x2", "f64")), (128, ("bf16", "bf16x2", "f32", "f64"))):
+        X = rng.standard_normal((n, r))
+        ref = None
+        for st in storages:
+            w, _ = phase_work(g, n, r, st)
+            f64_split = st == "f64" and r >= 12
+            if f64_split:
+                w = split_work(w, gen_counts(g), n, r, st)
+            nst = max(3, steps // 2) if (st == "f64" and r > 1) else max(steps, 20)
+            res, Y = time_variant(hm, torch, tree, g, st, X, nst, 2, 1, prof_steps=min(nst, 10))
+            ent = summarize(res, w, st, peaks, pipes, st in ("bf16", "bf16x2") and r >= 16,
+                            {"workload": "hodlr exp kernel n=262144 leaf=256 K=8 r=%d" % r, "storage": st,
+                             "x_dtype": X_DTYPE[st],
+                             "l2": "one matrix of %.0f MB per product (larger than L2)" % (res["generator_bytes"] / 1e6),
+                             "launches_per_step": res["launches_per_step"]})
+            if with_cpu:
+                Xe = X if st == "f64" else np.asarray(
+                    torch.from_numpy(X).to({"f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[st]])
+                    .to(torch.float64).numpy())
+                if r == 1:
+                    ent["err_vs_oracle"] = col_err(Y, OE.apply(t, ck, lk, Xe))
+                    ent["err_rows"] = "all %d (O(nK) recurrence)" % n
+                else:
+                    ent["err_vs_oracle"] = col_err(Y[rows], OM.matmat_rows(c, g, Xe, rows))
+                    ent["err_rows"] = "%d sampled rows (dense oracle)" % len(rows)
+            out["exp_n262144_r%d_%s" % (r, st)] = ent
+            del Y
+        del X
+    return out
+
+
 def main():
     args = parse()
     rank, local, world = dist_env()
     if args.impl == "reference":
         return run_reference(args)
+    if args.probe_sweep:
+        return probe_sweep() if rank == 0 else 0
     if args.workload == "batched":
         return run_batched(args) if rank == 0 else 0
     if args.workload == "serve":
@@ -611,54 +841,39 @@ def main():
     import paper_1909_07909_gb300 as hm
 
     peaks, peak_src = measured_peaks()
+    pipes = probe_pipes()
     tree, c, g, X = make_inputs()
-    g["_X"] = X
     prec = args.precision
-    gen_bytes_est = {"bf16": 45e6, "f32": 90e6, "bf16x2": 90e6, "f64": 180e6}[prec]
-    io = N_ * RHS * (16 if prec == "f64" else 8)
-    copies = args.copies or max(2, math.ceil(2.2 * 135.5e6 / (gen_bytes_est + io)))
+    w, gc = phase_work(g, N_, RHS, prec)
+    if prec == "f64":
+        w = split_work(w, gc, N_, RHS, prec)
+    est = {"bf16": 45e6, "f32": 90e6, "bf16x2": 90e6, "f64": 180e6}[prec] + N_ * RHS * (16 if prec == "f64" else 8)
+    copies = copies_for(est, args.copies)
 
     if world > 1:
         torch.distributed.barrier()
-    head, Yh = time_variant(hm, torch, tree, g, prec, args.steps, args.warmup, copies, True,
-                            clock_index=local, prof_steps=min(args.steps, 200), world=world)
+    head, Yh = time_variant(hm, torch, tree, g, prec, X, args.steps, args.warmup, copies, clock_index=local,
+                            prof_steps=min(args.steps, 20), world=world)
     # whole-job time: max over ranks of this rank's timed region
     ms_max = max_over_ranks(head["ms_total"], world, "cuda")
     value = job_throughput(head["bytes_per_step"], args.steps, ms_max, world)
 
-    # dominant kernel roofline (per-kernel durations from the profiled pass)
-    pb = phase_bytes(prec, c)
-    ph = head["phases"]
-    dom = max(range(4), key=lambda k: ph["ms"][k])
-    avg_ms = ph["ms"][dom] / max(ph["launches"][dom], 1)
-    achieved = pb[PHASES[dom]] / (avg_ms * 1e-3) / 1e9
-    kernel_key = "%s_%s" % (PHASES[dom], prec)
+    tc = prec in ("bf16", "bf16x2")
+    roof = roofline(w, head["phases"], prec, peaks, pipes, tc)
+    roof["kernel"] = KERNEL_NAMES.get((prec, roof["phase"]), "%s (%s storage)" % (roof["phase"], prec))
+    roof["traffic"] = traffic_for("hss_n65536:%s_%s" % (roof["phase"], prec))
+    step_flops = sum(v["flops"] for v in w.values())
     if prec == "f64":
-        flops = {"project": 2 * N_ * RANK * RHS, "tree": tree_flops(c), "tree_down": 0,
-                 "expand": 2 * (N_ * LEAF + N_ * RANK) * RHS}[PHASES[dom]]
-        roof = {"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": FP64_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "FP64 FMA probe (profiles/fma_peaks_probe.txt)"}
-    elif PHASES[dom] == "tree":
-        # FP32 small products: bound by the FMA pipes (and their shared-memory
-        # operands), not by HBM; the denominator is the scalar FFMA peak
-        roof = {"bound": "alu", "achieved": tree_flops(c) / (avg_ms * 1e-3) / 1e12, "peak": FP32_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "FP32 FMA probe (profiles/fma_peaks_probe.txt)"}
-    else:
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "peak_source": peak_src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = traffic_for(kernel_key)
-    roof["kernel"] = kernel_key
-    roof["ms_per_launch"] = avg_ms
-    roof["phase_ms_per_step"] = {PHASES[k]: ph["ms"][k] / ph["steps"] for k in range(4)}
-    roof["expand_frac_of_hbm"] = (pb["expand"] / (ph["ms"][3] / max(ph["launches"][3], 1) * 1e-3) / 1e9
-                                  / peaks["hbm_gbs"]) if ph["launches"][3] else None
+        roof["peak_nominal"] = FP64_NOMINAL_TFLOPS
+        roof["step"] = {"flops": step_flops, "achieved": step_flops / (ms_max / args.steps * 1e-3) / 1e12,
+                        "unit": "TFLOP/s"}
+        roof["step"]["frac"] = roof["step"]["achieved"] / roof["peak"]
+    ph = head["phases"]
+    roof["phase_ms_per_step"] = {PHASES[k]: ph["ms"][k] / ph["steps"] for k in range(len(PHASES))}
 
     out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16",
-                                                              "bf16x2": "bf16x2"}[prec],
-           "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": N_, "leaf": LEAF, "rank": RANK, "rhs": RHS, "storage": prec,
                       "x_dtype": X_DTYPE[prec], "y_dtype": "f64" if prec == "f64" else "f32",
                       "l2": "inputs larger than L2: %d rotating resident copies of %.1f MB" %
@@ -666,103 +881,95 @@ def main():
                       "generators": "leaf U,V orthonormal; R,B iid N(0,1/32) (variance); D=N(0,1)+8I; X=N(0,1)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "roofline": roof,
-           "gpu_launches": int(sum(ph["launches"]) * args.steps / ph["steps"]),
-           "clocks": head["clocks"]}
+           "gpu_launches": int(round(head["launches_per_step"] * args.steps)),
+           "clocks": head["clocks"],
+           "pipe_probe": pipes}
 
     if rank == 0:
-        out["e2e"] = e2e_host(hm, torch, tree, g, prec, max(5, min(50, args.steps // 4)))
+        out["e2e"] = e2e_host(hm, torch, tree, g, prec, X, max(5, min(20, args.steps)), copies)
         variants = {}
         ys = {prec: Yh}
         if not args.no_variants:
-            for v in ["f64", "f32", "bf16", "bf16x2"]:
+            for v in ["bf16", "bf16x2", "f32", "f64"]:
                 if v == prec:
                     continue
-                eb = {"bf16": 45e6, "f32": 90e6, "bf16x2": 90e6, "f64": 180e6}[v] + N_ * RHS * (16 if v == "f64" else 8)
-                cps = max(2, math.ceil(2.2 * 135.5e6 / eb))
-                st = 20 if v == "f64" else max(20, args.steps // 4)
-                r_, yv = time_variant(hm, torch, tree, g, v, st, 3, cps, True, prof_steps=min(st, 20))
+                wv, _ = phase_work(g, N_, RHS, v)
+                if v == "f64":
+                    wv = split_work(wv, gc, N_, RHS, v)
+                ev = {"bf16": 45e6, "f32": 90e6, "bf16x2": 90e6, "f64": 180e6}[v] + N_ * RHS * (16 if v == "f64" else 8)
+                st = max(10, args.steps) if v == "f64" else max(20, args.steps)
+                r_, yv = time_variant(hm, torch, tree, g, v, X, st, 3, copies_for(ev), prof_steps=min(st, 20))
                 ys[v] = yv
-                pbv = phase_bytes(v, c)
-                d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
-                am = r_["phases"]["ms"][d] / max(r_["phases"]["launches"][d], 1)
-                variants[v] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
-                               "dominant_kernel": PHASES[d],
-                               "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
-                                                     for k in range(4)}}
-                if pbv[PHASES[d]]:
-                    variants[v]["dominant_gbs"] = pbv[PHASES[d]] / (am * 1e-3) / 1e9
-            # the transposed product A^T X on the headline storage
-            st = max(20, args.steps // 4)
-            r_, yt = time_variant(hm, torch, tree, g, prec, st, 3, copies, True, prof_steps=min(st, 20),
-                                  form="transpose")
-            d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
-            variants["transpose"] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
-                                     "storage": prec, "dominant_kernel": PHASES[d],
-                                     "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
-                                                           for k in range(4)}}
-            # the same matrix in HODLR form (hss2hodlr on the device): more bytes, no tree recursion
-            r_, yh = time_variant(hm, torch, tree, g, prec, st, 3, copies, True, prof_steps=min(st, 20),
-                                  form="hodlr")
-            ys["hodlr_from_hss"] = yh
-            d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
-            variants["hodlr_from_hss"] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
-                                          "storage": prec, "generator_bytes": r_["generator_bytes"],
-                                          "dominant_kernel": PHASES[d],
-                                          "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] /
-                                                                r_["phases"]["steps"] for k in range(4)}}
-            # the Hadamard product of two HSS matrices of ranks 8 and 4 (rank 32), same tree and X
+                variants[v] = summarize(r_, wv, v, peaks, pipes, v in ("bf16", "bf16x2"),
+                                        {"steps": st, "x_dtype": X_DTYPE[v]})
+                variants[v]["time_ratio_vs_" + prec] = (ms_max / args.steps) / r_["ms_per_step"]
+            # derived matrices on BF16 storage: the transposed product, the
+            # HODLR form (hss2hodlr) and a Hadamard product (ranks 8 o 4)
+            st = max(20, args.steps)
+            ebf = 45e6 + N_ * RHS * 6
+            for form in ("transpose", "hodlr"):
+                r_, yf = time_variant(hm, torch, tree, g, "bf16", X, st, 3, copies_for(ebf), prof_steps=min(st, 20),
+                                      form=form)
+                key = "transpose" if form == "transpose" else "hodlr_from_hss"
+                ys[key] = yf
+                variants[key] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st, "storage": "bf16",
+                                 "generator_bytes": r_["generator_bytes"],
+                                 "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
+                                                       for k in range(len(PHASES))}}
             import workloads as W
             rng_h = W.rng_named("hss_n65536_m256_k32_r64", salt=11)
             gA8 = W.random_hss(rng_h, c, 8)
             gB4 = W.random_hss(rng_h, c, 4)
-            gA8["_X"] = X
-            r_, yhd = time_variant(hm, torch, tree, gA8, prec, st, 3, copies, True, prof_steps=min(st, 20),
+            r_, yhd = time_variant(hm, torch, tree, gA8, "bf16", X, st, 3, copies_for(ebf), prof_steps=min(st, 20),
                                    form="hadamard", g_b=gB4)
-            d = max(range(4), key=lambda k: r_["phases"]["ms"][k])
             variants["hadamard"] = {"value": r_["gbs"], "ms_per_step": r_["ms_per_step"], "steps": st,
-                                    "storage": prec, "ranks": "8 o 4 = 32", "generator_bytes": r_["generator_bytes"],
-                                    "dominant_kernel": PHASES[d],
-                                    "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] /
-                                                          r_["phases"]["steps"] for k in range(4)}}
+                                    "storage": "bf16", "ranks": "8 o 4 = 32", "generator_bytes": r_["generator_bytes"],
+                                    "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
+                                                          for k in range(len(PHASES))}}
+        if not args.no_workloads:
+            variants.update(run_workloads(hm, torch, np, peaks, pipes, args.steps, 3, not args.no_cpu and world == 1))
         if not args.no_cpu and world == 1:
+            # the timed CPU baseline: the fast tree product on every host core
+            secs, thr, Ycpu = cpu_fast_baseline(c, g, X)
+            b64 = fp64_step_bytes(c)
+            out["cpu_baseline"] = {"value": b64 / secs / 1e9, "unit": "GB/s", "cores": thr, "kind": "fast_matvec",
+                                   "ms_per_step": secs * 1e3,
+                                   "sample": "the whole product (n=65536, r=64, FP64): Fig. 4.1 in C++/OpenMP "
+                                             "(cpu_baseline/hm_cpu.cpp), best of 3 after a warm-up product"}
+            # the oracle itself, on a bounded sample
+            leaves = [0, 1, 127, 128, 200, 255][: max(1, args.cpu_leaves)]
+            dt, rows, Yo = cpu_oracle_sample(c, g, X, leaves)
+            frac = len(leaves) / len(c)
+            out["cpu_oracle"] = {"value": b64 / (dt / frac) / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
+                                 "kind": "oracle",
+                                 "sample": "%d of %d leaf row blocks of one product, %.2f s, scaled by %.1f"
+                                           % (len(leaves), len(c), dt, 1 / frac)}
+            errs = {"cpu_fast_matvec": col_err(Ycpu[rows], Yo)}
+            for v, Yv in ys.items():
+                if v in ("transpose", "hodlr_from_hss"):
+                    continue
+                errs[v] = col_err(Yv[rows], Yo)
+            errs["hodlr_from_hss"] = col_err(ys["hodlr_from_hss"][rows], Yo) if "hodlr_from_hss" in ys else None
+            out["err_vs_oracle"] = {"metric": "max over columns of ||y - y_oracle||_2/||y_oracle||_2 on %d "
+                                              "sampled rows" % len(rows), **errs}
+            for v in variants:
+                if v in errs and errs[v] is not None:
+                    variants[v]["err_vs_oracle"] = errs[v]
             if "hadamard" in variants:
                 from oracle import hadamard as OHD
                 from oracle import matmat as OMM
                 hrows = sorted(set([0, N_ - 1] + list(range(255, N_, N_ // 190))))[:192]
                 Yh_o = OMM.matmat_rows(c, OHD.hadamard_gens(c, gA8, gB4), X, hrows)
-                variants["hadamard"]["err_vs_oracle"] = float(np.max(
-                    np.linalg.norm(yhd[hrows] - Yh_o, axis=0) / np.linalg.norm(Yh_o, axis=0)))
+                variants["hadamard"]["err_vs_oracle"] = col_err(yhd[hrows], Yh_o)
                 variants["hadamard"]["err_rows"] = len(hrows)
-            if "transpose" in variants:
+            if "transpose" in ys:
                 from oracle import transpose as OTR
                 trows = sorted(set([0, N_ - 1] + list(range(255, N_, N_ // 190))))[:192]
                 Yt_o = OTR.matmat_transpose_rows(c, g, X, trows)
-                variants["transpose"]["err_vs_oracle"] = float(np.max(
-                    np.linalg.norm(yt[trows] - Yt_o, axis=0) / np.linalg.norm(Yt_o, axis=0)))
+                variants["transpose"]["err_vs_oracle"] = col_err(ys["transpose"][trows], Yt_o)
                 variants["transpose"]["err_rows"] = len(trows)
-            leaves = [0, 1, 127, 128, 200, 255][: max(1, args.cpu_leaves)]
-            dt, rows, Yo = cpu_oracle_sample(c, g, X, leaves)
-            frac = len(leaves) / len(c)
-            bytes64 = fp64_step_bytes(c)
-            est = dt / frac
-            out["cpu_baseline"] = {"value": bytes64 / est / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
-                                   "kind": "oracle",
-                                   "sample": "%d of %d leaf row blocks of one product, %.2f s, scaled by %.1f"
-                                             % (len(leaves), len(c), dt, 1 / frac)}
-            errs = {}
-            for v, Yv in ys.items():
-                num = np.linalg.norm(Yv[rows] - Yo, axis=0)
-                den = np.linalg.norm(Yo, axis=0)
-                errs[v] = float(np.max(num / den))
-            out["err_vs_oracle"] = {"metric": "max over columns of ||y - y_oracle||_2/||y_oracle||_2 on %d sampled rows"
-                                              % len(rows), **errs}
-            for v in variants:
-                if v in errs:
-                    variants[v]["err_vs_oracle"] = errs[v]
         if variants:
             out["variants"] = variants
-            if "f64" in variants and prec != "f64":
-                out["mixed_vs_fp64_speedup"] = value / world / variants["f64"]["value"]
         print(json.dumps(out))
     if world > 1:
         torch.distributed.barrier()

@@ -205,7 +205,7 @@ hm_status hm_hss_to_hodlr(const hm_matrix* S, hm_matrix** out);
 
 /* The Hadamard (entrywise) product C = A o B of two HODLR or two HSS
  * matrices on the same cluster tree, as a new matrix on the current device
- * (Sec. 4.5, Eq. 4.1, Fig. 4.3): D_C = D_A o D_B; every factor of C is the
+ * (Sec. 4.4, Eq. 4.1, Fig. 4.3): D_C = D_A o D_B; every factor of C is the
  * transpose Khatri-Rao product of A's and B's (row i = kron(row i of A's
  * factor, row i of B's), column a1 * k_B + a2); HSS couplings
  * B12_C = B12_A (x) B12_B, B21_C likewise, and each child's block of the
@@ -258,16 +258,17 @@ hm_status hm_hss_matmat(const hm_matrix* A, int64_t r, const void* X, int64_t ld
 /* Y = A X like hm_hodlr_matmat / hm_hss_matmat (chosen by the matrix's
  * kind), but allocating nothing.  This entry point has no counterpart in the
  * paper; it exists for callers that cannot allocate device memory where they
- * need a product: code recorded into a CUDA graph (allocation is not allowed
- * during stream capture), latency-bound serving loops that must not stall on
+ * need a product: latency-bound serving loops that must not stall on
  * cudaMalloc's implicit device synchronisation, and applications whose own
- * allocator owns all device memory.
+ * allocator (a caching allocator or a pool sized at start-up) owns all device
+ * memory, so that a library-side allocation could fail or fragment it.
  *   - The per-call scratch lives in one fixed 8 MiB device array compiled into
  *     the library (every GPU that loads the library holds it until the process
  *     exits).  A product whose scratch would exceed 8 MiB -- about
  *     (2L-1) * r * (rank terms) * 4 bytes, see hm_matrix_info -- is rejected
  *     with HM_EINVAL and a message naming the limit; split the columns of X.
- *   - X and Y must be device memory (host buffers would need staging memory).
+ *   - X and Y must be device memory (host buffers would need staging memory)
+ *     and must not overlap (HM_EINVAL).
  *   - The first call on a device looks up the array's device address; make
  *     that first call before any stream capture.
  *   - Every call shares the array and it keeps the previous call's contents;
@@ -281,6 +282,38 @@ hm_status hm_matmat_noalloc(const hm_matrix* A, int64_t r, const void* X, int64_
 /* Waits for `stream` and reports whether a device-side bounded wait of this
  * library timed out since the last call (HM_ETIMEOUT), then clears the flag. */
 hm_status hm_device_status(void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Failure detection and fault injection (not in the paper).  None of these */
+/* faults, traps or hangs the GPU: device waits give up after a time limit  */
+/* and report through hm_device_status; host failures are simulated.        */
+/* ---------------------------------------------------------------------- */
+
+/* Every bounded wait in this library's kernels (mbarrier phases of the TMA
+ * and tensor-core pipelines, the tree kernel's operator-ring slots) gives up
+ * after `ns` nanoseconds of %globaltimer, records an error code in the
+ * device status block, skips its stores and lets the kernel exit.  Default
+ * 2e9 (2 s); process-wide; applies to kernels launched after the call.
+ * 1e3 <= ns <= 6e10, else HM_EINVAL.  Short limits are for tests of the
+ * timeout path: a legitimate wait that outlasts the limit fails the product.
+ * Synchronous. */
+hm_status hm_set_device_wait_limit(uint64_t ns);
+hm_status hm_get_device_wait_limit(uint64_t* ns);
+
+/* Queues on `stream` one small self-test kernel whose two waits can never be
+ * satisfied: an mbarrier transaction that is never issued and a flag word
+ * that nothing sets.  Each gives up after the device wait limit and records
+ * its code (31, 32); the kernel then exits normally, so the context stays
+ * usable and the next hm_device_status on the stream returns HM_ETIMEOUT.
+ * It touches only its own shared memory and the library's status block. */
+hm_status hm_selftest_device_timeout(void* stream);
+
+/* Host-side fault injection: the next `count` device allocations made by the
+ * library (generators at create time, product scratch, host staging, batch
+ * and server buffers) fail as if the device were out of memory, so the call
+ * that needed them returns HM_ENOMEM and leaves no partial object behind.
+ * count = 0 disarms.  Process-wide. */
+hm_status hm_inject_alloc_failures(int32_t count);
 
 /* Selects the kernel family for later products on this matrix:
  * 0 = automatic (tensor cores when r is wide enough and storage is BF16 or
@@ -304,9 +337,11 @@ hm_status hm_matrix_profile(hm_matrix* A, int32_t enable);
 /* Device time accumulated per phase since the last read, in milliseconds,
  * and the number of launches: phase 0 = leaf projection (V^T X), 1 = tree
  * upsweep (HSS: translations R_V and couplings; HODLR: per-level sums),
- * 2 = HSS downsweep, 3 = leaf expansion.  Waits for the recorded events, then
+ * 2 = HSS downsweep, 3 = leaf expansion, 4 = the diagonal-block product D X
+ * when it runs as a launch of its own (FP64 storage with wide X; the
+ * expansion then adds E Z to it).  Waits for the recorded events, then
  * resets the accumulators. */
-hm_status hm_matrix_phase_times(hm_matrix* A, double ms[4], int64_t launches[4]);
+hm_status hm_matrix_phase_times(hm_matrix* A, double ms[5], int64_t launches[5]);
 
 /* ---------------------------------------------------------------------- */
 /* Batched products (the paper runs one product at a time; batching many   */
@@ -406,6 +441,18 @@ hm_status hm_serve_wait(hm_server* s, uint64_t ticket, int32_t timeout_ms);
 
 /* Non-blocking: HM_OK when the request has finished, HM_EBUSY while pending. */
 hm_status hm_serve_poll(hm_server* s, uint64_t ticket);
+
+/* Withdraws a request that is still queued: HM_OK (it will never run, Y is
+ * not written, its slot and budget are released and the ticket becomes
+ * unknown); HM_EBUSY when it is already running or finished (wait for it
+ * instead); HM_EINVAL for an unknown ticket. */
+hm_status hm_serve_cancel(hm_server* s, uint64_t ticket);
+
+/* pause = 1: the worker stops taking queued requests (products already
+ * launched finish); requests are still admitted and wait in the queue, as
+ * when a worker stalls.  pause = 0 resumes.  For tests of hm_serve_wait's
+ * timeout and of cancellation. */
+hm_status hm_serve_pause(hm_server* s, int32_t pause);
 
 hm_status hm_serve_stats(hm_server* s, hm_serve_stats_t* out);
 hm_status hm_serve_reset_stats(hm_server* s);

@@ -25,7 +25,7 @@ define, so the oracle is that definition written out in float64:
                   (A^T)(I, J) = A(J, I)^T and the product Y = A^T X.
 * ``convert``  -- hss2hodlr (Sec. 3.5): HODLR generators of an HSS matrix from
                   its explicit nested bases.
-* ``hadamard`` -- generators of A o B (Sec. 4.5, Eq. 4.1, Fig. 4.3): transpose
+* ``hadamard`` -- generators of A o B (Sec. 4.4, Eq. 4.1, Fig. 4.3): transpose
                   Khatri-Rao factors, Kronecker couplings and translations.
 * ``solve``    -- Y = A^{-1} B by a dense LU solve of the defining matrix
                   (Sec. 4.3), and the backward error of a candidate solution.

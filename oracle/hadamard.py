@@ -1,5 +1,5 @@
 """Hadamard product C = A o B of two HODLR or HSS matrices on the same
-cluster tree (Sec. 4.5, Eq. 4.1, Fig. 4.3).  Test infrastructure.
+cluster tree (Sec. 4.4, Eq. 4.1, Fig. 4.3).  Test infrastructure.
 
 For low-rank blocks, (U1 B1 V1^T) o (U2 B2 V2^T) = (U1 (.)^T U2)(B1 (x) B2)(V1 (.)^T V2)^T
 (Eq. 4.1), with (x) the Kronecker product and (.)^T the transpose Khatri-Rao
@@ -10,7 +10,7 @@ product: row i of C (.)^T D is kron(c_i, d_i).  So:
 * HSS: D_C = D_A o D_B; leaf bases U_C = U_A (.)^T U_B, V_C = V_A (.)^T V_B;
   couplings B12_C = B12_A (x) B12_B, B21_C likewise (Fig. 4.3 right).  The
   translation operators are stacked, R_U = [R_l; R_r], one block per child;
-  the derivation in Sec. 4.5 holds for each child's block, so the reading
+  the derivation in Sec. 4.4 holds for each child's block, so the reading
   here is R_U,C = [R_l,A (x) R_l,B; R_r,A (x) R_r,B] (and the same for R_V),
   not the Kronecker product of the two stacked matrices.
 

@@ -104,6 +104,12 @@ _decl("hm_serve_wait", C.c_int, vp, C.c_uint64, C.c_int32)
 _decl("hm_serve_poll", C.c_int, vp, C.c_uint64)
 _decl("hm_serve_stats", C.c_int, vp, C.POINTER(hm_serve_stats_t))
 _decl("hm_serve_reset_stats", C.c_int, vp)
+_decl("hm_serve_cancel", C.c_int, vp, C.c_uint64)
+_decl("hm_serve_pause", C.c_int, vp, C.c_int32)
+_decl("hm_set_device_wait_limit", C.c_int, C.c_uint64)
+_decl("hm_get_device_wait_limit", C.c_int, C.POINTER(C.c_uint64))
+_decl("hm_selftest_device_timeout", C.c_int, vp)
+_decl("hm_inject_alloc_failures", C.c_int, C.c_int32)
 _decl("hm_destroy", None, vp)
 
 

@@ -192,9 +192,11 @@ class Matrix:
         check(lib.hm_matrix_profile(self._h, 1 if enable else 0), "hm_matrix_profile")
 
     def phase_times(self):
-        """(ms[4], launches[4]) per phase (projection, tree up, HSS down, expansion) since the last read."""
-        ms = (C.c_double * 4)()
-        n = (C.c_int64 * 4)()
+        """(ms[5], launches[5]) per phase since the last read: projection, tree up,
+        HSS down, expansion, and the diagonal-block product when it is a launch
+        of its own (FP64 with wide X)."""
+        ms = (C.c_double * 5)()
+        n = (C.c_int64 * 5)()
         check(lib.hm_matrix_phase_times(self._h, ms, n), "hm_matrix_phase_times")
         return list(ms), list(n)
 
@@ -321,6 +323,18 @@ class Server:
         check(st, "hm_serve_poll")
         return True
 
+    def cancel(self, ticket):
+        """True if the queued request was withdrawn, False if it already runs or ran."""
+        st = lib.hm_serve_cancel(self._h, int(ticket))
+        if st == L.HM_EBUSY:
+            return False
+        check(st, "hm_serve_cancel")
+        return True
+
+    def pause(self, paused=True):
+        """Stop (True) or resume (False) the worker's intake of queued requests."""
+        check(lib.hm_serve_pause(self._h, 1 if paused else 0), "hm_serve_pause")
+
     def stats(self):
         sst = L.hm_serve_stats_t()
         check(lib.hm_serve_stats(self._h, C.byref(sst)), "hm_serve_stats")
@@ -346,3 +360,24 @@ def colmajor(t):
 
 def device_status(stream=None):
     check(lib.hm_device_status(vp(stream) if stream else None), "hm_device_status")
+
+
+def set_device_wait_limit(ns):
+    """Device-side bounded waits give up after `ns` nanoseconds (default 2e9)."""
+    check(lib.hm_set_device_wait_limit(int(ns)), "hm_set_device_wait_limit")
+
+
+def device_wait_limit():
+    v = C.c_uint64()
+    check(lib.hm_get_device_wait_limit(C.byref(v)), "hm_get_device_wait_limit")
+    return v.value
+
+
+def selftest_device_timeout(stream=None):
+    """Queues the kernel whose bounded waits always run out (see hm.h)."""
+    check(lib.hm_selftest_device_timeout(vp(stream) if stream else None), "hm_selftest_device_timeout")
+
+
+def inject_alloc_failures(count):
+    """The next `count` device allocations of the library fail (HM_ENOMEM)."""
+    check(lib.hm_inject_alloc_failures(int(count)), "hm_inject_alloc_failures")

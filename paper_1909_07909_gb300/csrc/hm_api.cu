@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -47,21 +48,41 @@ static hm_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 // ----------------------------------------------------------------------------
-// Per-device state: the error word of bounded device waits.
+// Per-device state: the status block of bounded device waits (the error word,
+// then the wait limit in nanoseconds; see DeviceStatusBlock).
 // ----------------------------------------------------------------------------
 
 static std::mutex g_dev_mu;
 static std::unordered_map<int, int*> g_dev_err;
+static uint64_t g_wait_ns = kDefaultWaitNs;
 
 int* device_error_word(int dev) {
   std::lock_guard<std::mutex> lk(g_dev_mu);
   auto it = g_dev_err.find(dev);
   if (it != g_dev_err.end()) return it->second;
-  int* p = nullptr;
-  if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
-  if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
-  g_dev_err[dev] = p;
-  return p;
+  DeviceStatusBlock* p = nullptr;
+  if (cudaMalloc(&p, sizeof(DeviceStatusBlock)) != cudaSuccess) return nullptr;
+  DeviceStatusBlock h;
+  h.err = 0;
+  h.flag = 0;
+  h.wait_ns = g_wait_ns;
+  if (cudaMemcpy(p, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+  g_dev_err[dev] = &p->err;
+  return &p->err;
+}
+
+// Host-side fault injection: the next g_alloc_fail device allocations fail.
+static std::atomic<int> g_alloc_fail{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int left = g_alloc_fail.load();
+  while (left > 0) {
+    if (g_alloc_fail.compare_exchange_weak(left, left - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(p, bytes);
 }
 
 // ----------------------------------------------------------------------------
@@ -258,7 +279,7 @@ static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 static hm_status upload(const void* h, size_t bytes, void** d, size_t* total) {
   *d = nullptr;
   if (bytes == 0) return HM_OK;
-  HM_CUDA(cudaMalloc(d, bytes), "cudaMalloc (generators)");
+  HM_CUDA(dev_malloc(d, bytes), "cudaMalloc (generators)");
   HM_CUDA(cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice), "cudaMemcpy (generators)");
   *total += bytes;
   return HM_OK;
@@ -608,9 +629,11 @@ size_t scratch_elems(const MatView& mv, int64_t r) {
   return nodes * r * (mv.Kp + 2 * static_cast<size_t>(mv.Ke)) + nodes * r8 * mv.Ke;
 }
 
-size_t counter_count(const MatView& mv, int64_t r) {
+size_t tree_counter_count(const MatView& mv, int64_t r) {
   return static_cast<size_t>(std::max(mv.L - 1, 1)) * static_cast<size_t>(std::max<int64_t>(r, 1));
 }
+
+size_t counter_count(const MatView& mv, int64_t r) { return tree_counter_count(mv, r) + 8; }
 
 hm_status ensure_scratch(hm_matrix* A, int64_t r) {
   if (r <= A->r_cap && A->d_ws) return HM_OK;
@@ -624,8 +647,8 @@ hm_status ensure_scratch(hm_matrix* A, int64_t r) {
   A->r_cap = 0;
   const size_t wb = std::max<size_t>(scratch_elems(mv, r) * cs, 256);
   const size_t cb = counter_count(mv, r) * sizeof(int);
-  cudaError_t e = cudaMalloc(&A->d_ws, wb);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&A->d_cnt), cb);
+  cudaError_t e = dev_malloc(&A->d_ws, wb);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&A->d_cnt), cb);
   if (e == cudaSuccess) e = cudaMemset(A->d_cnt, 0, cb);
   if (e == cudaSuccess) e = cudaMemset(A->d_ws, 0, wb);
   if (dev_prev != A->device) cudaSetDevice(dev_prev);
@@ -704,7 +727,7 @@ hm_status run_product(const hm_matrix* Ac, int want_kind, int64_t r, const void*
     const size_t need = static_cast<size_t>(n) * r * (xs + ys) + 256;
     if (A->io_cap < need) {
       if (A->d_io) { cudaStreamSynchronize(s); cudaFree(A->d_io); A->d_io = nullptr; A->io_cap = 0; }
-      HM_CUDA(cudaMalloc(&A->d_io, need), "cudaMalloc (host staging)");
+      HM_CUDA(dev_malloc(&A->d_io, need), "cudaMalloc (host staging)");
       A->io_cap = need;
     }
     char* base = static_cast<char*>(A->d_io);
@@ -740,6 +763,30 @@ hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int
       default: return simt_phase_bf16x2(ph, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
     }
   };
+  if (f64_tiled(mv, r)) {
+    // FP64, wide blocks: projection -> tree -> D X (starts while the tree runs)
+    // -> Y += E Z, every phase bound by the FP64 pipe (k_f64.cu)
+    prof_mark(ws.prof, 0, true, s);
+    hm_status st = f64_leaf_phase(0, mv, ws, r, X, ldx, Y, ldy, s, false, 0);
+    prof_mark(ws.prof, 0, false, s);
+    if (st != HM_OK) return st;
+    st = launch_tree_cluster(A, mv, ws, r, s, true);
+    A->tree_last_cluster = (st == HM_OK);
+    if (st == HM_EUNSUPPORTED) {
+      st = phase(1, true);
+      if (st != HM_OK) return st;
+      st = phase(2, true);
+    }
+    if (st != HM_OK) return st;
+    prof_mark(ws.prof, 4, true, s);
+    st = f64_leaf_phase(1, mv, ws, r, X, ldx, Y, ldy, s, true, 0);
+    prof_mark(ws.prof, 4, false, s);
+    if (st != HM_OK) return st;
+    prof_mark(ws.prof, 3, true, s);
+    st = f64_leaf_phase(2, mv, ws, r, X, ldx, Y, ldy, s, true, 0);
+    prof_mark(ws.prof, 3, false, s);
+    return st;
+  }
   hm_status st = HM_EUNSUPPORTED;
   if (use_tensor_cores(A, r)) st = launch_project_tc(A, mv, ws, r, X, ldx, xt, s, false);
   if (st == HM_EUNSUPPORTED) st = phase(0, false);
@@ -785,7 +832,7 @@ void EventProf::mark(int phase, bool start, cudaStream_t s) {
   }
 }
 
-hm_status EventProf::read(double ms[4], int64_t launches[4]) {
+hm_status EventProf::read(double ms[kPhaseSlots], int64_t launches[kPhaseSlots]) {
   for (auto& r : recs_) {
     HM_CUDA(cudaEventSynchronize(r.b), "event synchronize");
     float t = 0.f;
@@ -796,7 +843,7 @@ hm_status EventProf::read(double ms[4], int64_t launches[4]) {
     pool_.push_back(r.b);
   }
   recs_.clear();
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < kPhaseSlots; ++i) {
     ms[i] = ms_[i];
     launches[i] = n_[i];
     ms_[i] = 0;
@@ -825,11 +872,11 @@ extern "C" hm_status hm_matrix_profile(hm_matrix* A, int32_t enable) {
   return HM_OK;
 }
 
-extern "C" hm_status hm_matrix_phase_times(hm_matrix* A, double ms[4], int64_t launches[4]) {
+extern "C" hm_status hm_matrix_phase_times(hm_matrix* A, double ms[5], int64_t launches[5]) {
   if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
   if (!ms || !launches) return fail(HM_EINVAL, "output arrays are NULL");
   if (!A->prof) {
-    for (int i = 0; i < 4; ++i) { ms[i] = 0; launches[i] = 0; }
+    for (int i = 0; i < kPhaseSlots; ++i) { ms[i] = 0; launches[i] = 0; }
     return HM_OK;
   }
   return static_cast<EventProf*>(A->prof)->read(ms, launches);
@@ -869,6 +916,46 @@ extern "C" hm_status hm_device_status(void* stream) {
     return fail(HM_ETIMEOUT, "a device-side bounded wait timed out (code %d)", v);
   }
   return HM_OK;
+}
+
+extern "C" hm_status hm_set_device_wait_limit(uint64_t ns) {
+  if (ns < 1000 || ns > 60000000000ull) return fail(HM_EINVAL, "wait limit must be in [1e3, 6e10] ns");
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  g_wait_ns = ns;
+  int dev_prev = -1;
+  cudaGetDevice(&dev_prev);
+  for (auto& kv : g_dev_err) {
+    cudaSetDevice(kv.first);
+    DeviceStatusBlock* b = reinterpret_cast<DeviceStatusBlock*>(kv.second);
+    const cudaError_t e = cudaMemcpy(&b->wait_ns, &ns, sizeof(ns), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      if (dev_prev >= 0) cudaSetDevice(dev_prev);
+      return cuda_fail(e, "write the device wait limit");
+    }
+  }
+  if (dev_prev >= 0) cudaSetDevice(dev_prev);
+  return HM_OK;
+}
+
+extern "C" hm_status hm_get_device_wait_limit(uint64_t* ns) {
+  if (!ns) return fail(HM_EINVAL, "ns is NULL");
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  *ns = g_wait_ns;
+  return HM_OK;
+}
+
+extern "C" hm_status hm_inject_alloc_failures(int32_t count) {
+  if (count < 0) return fail(HM_EINVAL, "count < 0");
+  g_alloc_fail.store(count);
+  return HM_OK;
+}
+
+extern "C" hm_status hm_selftest_device_timeout(void* stream) {
+  int dev = 0;
+  HM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  int* w = device_error_word(dev);
+  if (!w) return fail(HM_ECUDA, "no device status block");
+  return launch_selftest_timeout(reinterpret_cast<DeviceStatusBlock*>(w), static_cast<cudaStream_t>(stream));
 }
 
 extern "C" void hm_destroy(void* any) {

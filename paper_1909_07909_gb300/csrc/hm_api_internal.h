@@ -29,6 +29,10 @@ uint16_t f64_to_bf16(double a);
 double bf16_to_f64(uint16_t h);
 size_t storage_bytes(int st);
 int* device_error_word(int dev);
+// cudaMalloc, unless a failure was injected with hm_inject_alloc_failures.
+cudaError_t dev_malloc(void** p, size_t bytes);
+// The timeout self-test kernel (hm_fault.cu).
+hm_status launch_selftest_timeout(DeviceStatusBlock* b, cudaStream_t s);
 const double* host_block(const double* p, size_t count, std::vector<double>& tmp);
 
 }  // namespace hmi
@@ -96,20 +100,22 @@ int64_t node_start(const hm_tree* t, int q);
 int64_t node_end(const hm_tree* t, int q);
 hm_status ensure_scratch(hm_matrix* A, int64_t r);
 
-// CUDA-event timing of the phases of the products of one matrix.
+// CUDA-event timing of the phases of the products of one matrix (slots as in
+// hm_matrix_phase_times).
+constexpr int kPhaseSlots = 5;
 class EventProf : public Prof {
  public:
   void mark(int phase, bool start, cudaStream_t s) override;
-  hm_status read(double ms[4], int64_t launches[4]);
+  hm_status read(double ms[kPhaseSlots], int64_t launches[kPhaseSlots]);
   ~EventProf() override;
 
  private:
   struct Rec { int phase; cudaEvent_t a, b; };
   std::vector<Rec> recs_;
   std::vector<cudaEvent_t> pool_;
-  cudaEvent_t open_[4] = {nullptr, nullptr, nullptr, nullptr};
-  double ms_[4] = {0, 0, 0, 0};
-  int64_t n_[4] = {0, 0, 0, 0};
+  cudaEvent_t open_[kPhaseSlots] = {};
+  double ms_[kPhaseSlots] = {};
+  int64_t n_[kPhaseSlots] = {};
   cudaEvent_t get();
 };
 Scratch scratch_of(const hm_matrix* A, int64_t r);

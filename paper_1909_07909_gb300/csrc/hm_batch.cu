@@ -205,11 +205,11 @@ static hm_status build_plan(hm_batch* b) {
     else batch_set_smem(p, b->smem[p]);
   }
   // upload
-  cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(BatchJob) * std::max(b->count, 1));
+  cudaError_t e = dev_malloc(reinterpret_cast<void**>(&b->d_jobs), sizeof(BatchJob) * std::max(b->count, 1));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_jobs, b->jobs.data(), sizeof(BatchJob) * b->count, cudaMemcpyHostToDevice);
   for (int p = 0; p < BP_COUNT && e == cudaSuccess; ++p) {
     if (b->items[p].empty()) continue;
-    e = cudaMalloc(&b->d_items[p], sizeof(BItem) * b->items[p].size());
+    e = dev_malloc(reinterpret_cast<void**>(&b->d_items[p]), sizeof(BItem) * b->items[p].size());
     if (e == cudaSuccess)
       e = cudaMemcpy(b->d_items[p], b->items[p].data(), sizeof(BItem) * b->items[p].size(), cudaMemcpyHostToDevice);
   }
@@ -359,10 +359,10 @@ extern "C" hm_status hm_batch_create(hm_matrix* const* A, const int64_t* r, int3
     total += ((scratch_elems(mv, r[j]) * 4 + 255) / 256) * 256 + ((counter_count(mv, r[j]) * sizeof(int) + 255) / 256) * 256;
   }
   b->scratch_bytes = std::max<size_t>(total, 256);
-  cudaError_t e = cudaMalloc(&b->d_scratch, b->scratch_bytes);
+  cudaError_t e = dev_malloc(reinterpret_cast<void**>(&b->d_scratch), b->scratch_bytes);
   if (e == cudaSuccess) e = cudaMemset(b->d_scratch, 0, b->scratch_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_io, sizeof(BatchIO) * count);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * BATCH_MAPS * count);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&b->d_io), sizeof(BatchIO) * count);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&b->d_maps), sizeof(CUtensorMap) * BATCH_MAPS * count);
   if (e == cudaSuccess) {
     std::vector<CUtensorMap> maps(BATCH_MAPS * count);
     for (int j = 0; j < count; ++j) {

@@ -247,7 +247,7 @@ extern "C" hm_status hm_hss_to_hodlr(const hm_matrix* S, hm_matrix** out) {
                     {&H->d_W_lo, split ? w_elems * 2 : 0}};
   for (const Alloc& a : allocs) {
     if (a.bytes == 0) continue;
-    const cudaError_t e = cudaMalloc(a.p, a.bytes);
+    const cudaError_t e = dev_malloc(reinterpret_cast<void**>(a.p), a.bytes);
     if (e != cudaSuccess)
       return convert_fail(H, e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA, "cudaMalloc (hss2hodlr)", e);
     dev_bytes += a.bytes;

@@ -1,6 +1,6 @@
 // hm_hadamard: C = A o B (entrywise product) of two HODLR or two HSS matrices
 // on the same cluster tree, built on the device from A's and B's storage
-// (Sec. 4.5, Eq. 4.1, Fig. 4.3).
+// (Sec. 4.4, Eq. 4.1, Fig. 4.3).
 //
 // For low-rank blocks (U1 B1 V1^T) o (U2 B2 V2^T) = (U1 (.)^T U2)(B1 (x) B2)(V1 (.)^T V2)^T,
 // where (x) is the Kronecker product and (.)^T the transpose Khatri-Rao
@@ -318,7 +318,7 @@ extern "C" hm_status hm_hadamard(const hm_matrix* A, const hm_matrix* B, hm_matr
                     {&M->d_B21, b_b, false}};
   for (const Alloc& al : allocs) {
     if (al.bytes == 0) continue;
-    cudaError_t e = cudaMalloc(al.p, al.bytes);
+    cudaError_t e = dev_malloc(reinterpret_cast<void**>(al.p), al.bytes);
     if (e == cudaSuccess && al.zero) e = cudaMemset(*al.p, 0, al.bytes);   // padding columns and rows
     if (e != cudaSuccess)
       return hadamard_fail(M, e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA, "allocation (hadamard)", e);

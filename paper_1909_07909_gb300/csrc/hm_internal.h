@@ -64,7 +64,8 @@ struct MatView {
   int koff[kMaxDepth + 2];  // HODLR offset of level l inside the Ke block
 };
 
-// Optional per-kernel event timing (phase 0 project, 1 tree upsweep, 2 HSS downsweep, 3 expand).
+// Optional per-kernel event timing (phase 0 project, 1 tree upsweep, 2 HSS
+// downsweep, 3 expand, 4 FP64 diagonal-block product run apart from the expansion).
 struct Prof {
   virtual void mark(int phase, bool start, cudaStream_t s) = 0;
   virtual ~Prof() {}
@@ -72,6 +73,24 @@ struct Prof {
 
 inline void prof_mark(Prof* p, int phase, bool start, cudaStream_t s) {
   if (p) p->mark(phase, start, s);
+}
+
+// The per-device status block of the library's bounded device waits: the
+// error word a kernel sets when a wait gives up (read and cleared by
+// hm_device_status), a flag word that nothing in the product path sets (the
+// timeout self-test waits on it), and the wait limit in nanoseconds
+// (hm_set_device_wait_limit).  Kernels receive a pointer to `err`.
+struct DeviceStatusBlock {
+  int err;
+  int flag;
+  unsigned long long wait_ns;
+};
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+
+// The wait limit of the status block whose error word is `err` (the default
+// when there is none).
+__device__ __forceinline__ uint64_t wait_limit_ns(const int* err) {
+  return err ? reinterpret_cast<const volatile DeviceStatusBlock*>(err)->wait_ns : kDefaultWaitNs;
 }
 
 struct Scratch {
@@ -96,9 +115,24 @@ HM_SIMT_PHASE_DECL(bf16)
 HM_SIMT_PHASE_DECL(bf16x2)
 #undef HM_SIMT_PHASE_DECL
 
-// Scratch element counts for r columns (in compute-type elements) and counter count.
+// Scratch element counts for r columns (in compute-type elements) and counter
+// count: the tree kernels' arrival counters, then 8 work counters of the FP64
+// leaf kernels.
 size_t scratch_elems(const MatView& mv, int64_t r);
+size_t tree_counter_count(const MatView& mv, int64_t r);
 size_t counter_count(const MatView& mv, int64_t r);
+
+// FP64 storage with at least this many right-hand sides runs the register-tiled
+// FP64 leaf kernels (k_f64.cu); narrower blocks run the SIMT row engine.
+constexpr int kF64TiledMinR = 12;
+bool f64_tiled(const MatView& mv, int64_t r);
+inline int* f64_counters(const Scratch& ws, const MatView& mv, int64_t r) {
+  return ws.cnt + tree_counter_count(mv, r);
+}
+// One FP64 leaf phase: 0 projection (x-hat / per-level V^T X), 1 diagonal-block
+// product Y = D X, 2 expansion Y += E Z.  grid_cap > 0 limits the persistent grid.
+hm_status f64_leaf_phase(int which, const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx,
+                         void* Y, int64_t ldy, cudaStream_t st, bool pdl, int grid_cap);
 
 void set_error(const char* fmt, ...);
 

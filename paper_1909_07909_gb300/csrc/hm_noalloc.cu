@@ -2,14 +2,14 @@
 // statically allocated device array instead of memory the library allocates.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// product: code that records the product into a CUDA graph (allocation calls
-// are not allowed while a stream is being captured), real-time or serving
-// loops that must not stall on cudaMalloc's implicit device synchronisation,
-// and applications that hand every byte of the GPU to their own allocator.
-// This entry point lets them run the product with no allocation at all: the
-// matrix is created beforehand, X and Y are the caller's device buffers, and
-// the per-call scratch (tree intermediates and arrival counters) lives in the
-// array below.
+// product: real-time or serving loops that must not stall on cudaMalloc's
+// implicit device synchronisation, and applications that hand every byte of
+// the GPU to their own allocator (a framework's caching allocator, a memory
+// pool sized at start-up), where a library-side cudaMalloc can fail or
+// fragment that pool.  This entry point lets them run the product with no
+// allocation at all: the matrix is created beforehand, X and Y are the
+// caller's device buffers, and the per-call scratch (tree intermediates and
+// arrival counters) lives in the array below.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -78,6 +78,16 @@ extern "C" hm_status hm_matmat_noalloc(const hm_matrix* Ac, int64_t r, const voi
   }
   if (r == 0 || n == 0) return HM_OK;
   if (!X || !Y) { set_error("X or Y is NULL"); return HM_EINVAL; }
+  {
+    // the leaf expansion writes Y while the diagonal-block term still reads X
+    const size_t xs = (xt == HM_F64) ? 8 : (xt == HM_F32) ? 4 : 2;
+    const size_t ys = (yt == HM_F64) ? 8 : 4;
+    const char* x0 = static_cast<const char*>(X);
+    const char* x1 = x0 + ((r - 1) * ldx + n) * xs;
+    const char* y0 = static_cast<const char*>(Y);
+    const char* y1 = y0 + ((r - 1) * ldy + n) * ys;
+    if (x0 < y1 && y0 < x1) { set_error("X and Y overlap"); return HM_EINVAL; }
+  }
   const size_t need = noalloc_required_bytes(A, r);
   if (need > kNoAllocScratchBytes) {
     set_error("hm_matmat_noalloc: this product needs %zu bytes of scratch, above the fixed %zu-byte limit "

@@ -98,6 +98,7 @@ struct hm_server {
   uint64_t next_ticket = 1;
   std::thread worker;
   std::atomic<bool> stop{false};
+  std::atomic<bool> paused{false};   // hm_serve_pause: the worker takes no queued request
 };
 
 namespace hmi {
@@ -209,20 +210,20 @@ static void worker_main(hm_server* s) {
     std::vector<std::pair<int, std::vector<uint64_t>>> groups;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (s->queue.empty()) {
+      if (s->queue.empty() || s->paused.load()) {
         if (s->inflight.empty())
           s->cv_work.wait_for(lk, std::chrono::microseconds(200));
         else
           s->cv_work.wait_for(lk, std::chrono::microseconds(10));
-        if (s->queue.empty()) continue;
+        if (s->queue.empty() || s->paused.load()) continue;
       }
       std::unordered_map<int, size_t> at;
       std::unordered_map<int, int64_t> cols;
-      std::deque<uint64_t> rest;
       while (!s->queue.empty()) {
         const uint64_t t = s->queue.front();
         s->queue.pop_front();
-        const SrvReq& q = s->reqs[t];
+        SrvReq& q = s->reqs[t];
+        q.state = RQ_RUNNING;   // taken: no longer cancellable
         auto f = at.find(q.id);
         if (f == at.end() || cols[q.id] + q.r > s->r_cap) {
           at[q.id] = groups.size();
@@ -315,7 +316,7 @@ extern "C" hm_status hm_serve_register(hm_server* s, hm_matrix* A, int32_t* id) 
   M.A = A;
   M.stream = static_cast<int>(s->mats.size() % s->streams.size());
   hm_status st = ensure_scratch(A, s->r_cap);
-  if (st == HM_OK && (cudaMalloc(&M.xbuf, bufs / 2) != cudaSuccess || cudaMalloc(&M.ybuf, bufs / 2) != cudaSuccess))
+  if (st == HM_OK && (dev_malloc(reinterpret_cast<void**>(&M.xbuf), bufs / 2) != cudaSuccess || dev_malloc(reinterpret_cast<void**>(&M.ybuf), bufs / 2) != cudaSuccess))
     st = sfail(HM_ENOMEM, "merge buffers");
   if (dev_prev != s->device) cudaSetDevice(dev_prev);
   if (st != HM_OK) {
@@ -390,6 +391,28 @@ extern "C" hm_status hm_serve_poll(hm_server* s, uint64_t ticket) {
   const hm_status st = f->second.status;
   s->reqs.erase(f);
   return st;
+}
+
+extern "C" hm_status hm_serve_cancel(hm_server* s, uint64_t ticket) {
+  if (!s || s->magic != kMagicServer) return sfail(HM_EINVAL, "not a server handle");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto f = s->reqs.find(ticket);
+  if (f == s->reqs.end()) return sfail(HM_EINVAL, "unknown ticket %llu", static_cast<unsigned long long>(ticket));
+  if (f->second.state != RQ_QUEUED)
+    return sfail(HM_EBUSY, "request %llu is already running or finished", static_cast<unsigned long long>(ticket));
+  auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
+  if (q != s->queue.end()) s->queue.erase(q);
+  s->pending -= 1;
+  s->transient -= f->second.transient;
+  s->reqs.erase(f);
+  return HM_OK;
+}
+
+extern "C" hm_status hm_serve_pause(hm_server* s, int32_t pause) {
+  if (!s || s->magic != kMagicServer) return sfail(HM_EINVAL, "not a server handle");
+  s->paused.store(pause != 0);
+  s->cv_work.notify_all();
+  return HM_OK;
 }
 
 extern "C" hm_status hm_serve_stats(hm_server* s, hm_serve_stats_t* out) {

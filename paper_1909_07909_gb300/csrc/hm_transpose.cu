@@ -177,7 +177,7 @@ extern "C" hm_status hm_matrix_transpose(const hm_matrix* A, hm_matrix** out) {
                     {&T->d_B21, b_b}};
   for (const Alloc& a : allocs) {
     if (a.bytes == 0) continue;
-    const cudaError_t e = cudaMalloc(a.p, a.bytes);
+    const cudaError_t e = dev_malloc(reinterpret_cast<void**>(a.p), a.bytes);
     if (e != cudaSuccess)
       return transpose_fail(T, e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA, "cudaMalloc (transpose)", e);
     dev_bytes += a.bytes;

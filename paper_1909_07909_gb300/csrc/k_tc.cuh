@@ -19,7 +19,8 @@
 //  * Split BF16: A = A_hi + A_lo and B = B_hi + B_lo; acc0 += A_hi B_hi,
 //    acc1 += A_hi B_lo + A_lo B_hi (the lo*lo term is dropped), and the
 //    epilogue adds the two accumulators in FP64.
-//  * Every wait is bounded (2 s of %globaltimer); on expiry the kernel sets
+//  * Every wait is bounded (the device wait limit, 2 s of %globaltimer by
+//    default, hm_set_device_wait_limit); on expiry the kernel sets
 //    the library's device error word, skips its stores and still releases
 //    its tensor memory.
 #include <cuda.h>
@@ -35,7 +36,6 @@ namespace hmi {
 constexpr int TC_M = 128;
 constexpr int TC_KC = 64;
 constexpr int TC_MAX_STAGES = 4;
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -67,13 +67,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; on expiry records `code` and returns false.
+// Bounded wait on an mbarrier phase; after the wait limit of the status block
+// of `err` (%globaltimer) records `code` there and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
+  const uint64_t limit = wait_limit_ns(err);
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (gtimer() - t0 > TC_WAIT_NS) {
+    if (gtimer() - t0 > limit) {
       if (err) atomicExch(err, code);
       return false;
     }

@@ -24,8 +24,9 @@
 // ring runs ahead across level boundaries.  Every sum runs in the same order
 // as in the level kernels (fma over j from zero, then + y_c; paired FMAs
 // round each half exactly like fmaf), so both give identical bits.  Every
-// wait is bounded (2 s of %globaltimer): on expiry the kernel records an
-// error code in the library's error word and stops waiting.
+// wait is bounded (the library's device wait limit, 2 s of %globaltimer by
+// default): on expiry the kernel records an error code in the library's
+// error word and stops waiting.
 #include <type_traits>
 
 #include "hm_api_internal.h"
@@ -322,8 +323,9 @@ __device__ __forceinline__ void ring_acquire(const Ring& R, int k, int* err) {
     bool ok = (*held == k);
     if (!ok) {
       const uint64_t t0 = gtimer();
+      const uint64_t limit = wait_limit_ns(err);
       while (!(ok = (*held == k))) {
-        if (gtimer() - t0 > TC_WAIT_NS) {
+        if (gtimer() - t0 > limit) {
           atomicExch(err, 22);
           break;
         }
@@ -851,8 +853,11 @@ static bool tree_pick(const MatView& mv, int64_t r, TreeShape* out) {
   const int smax = mv.p < TREE_MAX_S ? mv.p : TREE_MAX_S;
   for (int s = (smax >= 3 ? 3 : smax); s <= smax; ++s) {
     for (int rc = 1; rc <= 8; rc *= 2) {
-      // a deep ring at one CTA per SM, or a shallower one that lets two share an SM
-      const uint32_t budgets[2] = {227u * 1024 - 512, 113u * 1024 - 256};
+      // a deep ring at one CTA per SM, or a shallower one that lets two share
+      // an SM; for FP64 the deep ring leaves room for a block of the
+      // diagonal-block product, which runs beside the tree (k_f64.cu)
+      const uint32_t deep = (mv.storage == HM_F64) ? 188u * 1024 : 227u * 1024 - 512;
+      const uint32_t budgets[2] = {deep, 113u * 1024 - 256};
       for (uint32_t budget : budgets) {
         const int ns = tree_ring<C>(mv, rc, s, budget);
         if (ns == 0) continue;

@@ -127,3 +127,16 @@ def test_package_does_not_reach_the_oracle():
             continue
         src = open(path, errors="replace").read()
         assert not re.search(r"\bimport\s+oracle|\bfrom\s+oracle|oracle/", src), path
+
+
+def test_fault_injection_entry_points_check_arguments_before_gpu_work():
+    assert L.lib.hm_set_device_wait_limit(10) == L.HM_EINVAL            # below 1 us
+    assert L.lib.hm_set_device_wait_limit(10 ** 12) == L.HM_EINVAL      # above 60 s
+    v = C.c_uint64()
+    assert L.lib.hm_get_device_wait_limit(C.byref(v)) == L.HM_OK
+    assert v.value == 2_000_000_000
+    assert L.lib.hm_get_device_wait_limit(None) == L.HM_EINVAL
+    assert L.lib.hm_inject_alloc_failures(-1) == L.HM_EINVAL
+    assert L.lib.hm_inject_alloc_failures(0) == L.HM_OK
+    assert L.lib.hm_serve_cancel(None, 1) == L.HM_EINVAL
+    assert L.lib.hm_serve_pause(None, 1) == L.HM_EINVAL

@@ -596,7 +596,7 @@ def test_hss_to_hodlr_planted_mistakes(monkeypatch, plant):
 
 
 # --------------------------------------------------------------------------
-# Hadamard product (Sec. 4.5, Eq. 4.1, Fig. 4.3)
+# Hadamard product (Sec. 4.4, Eq. 4.1, Fig. 4.3)
 # --------------------------------------------------------------------------
 
 def test_khatri_rao_t_definition():
