@@ -70,8 +70,11 @@ def parse():
     ap.add_argument("--no-workloads", action="store_true", help="skip the n=4096 and n=262144 workloads")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-leaves", type=int, default=6, help="leaf row blocks in the CPU oracle sample")
-    ap.add_argument("--workload", default="hss", choices=["hss", "batched", "serve"],
-                    help="hss: the HSS n=65536 headline; batched: 512 uneven matrices; serve: Poisson requests")
+    ap.add_argument("--workload", default="hss", choices=["hss", "exp", "hodlr4096", "batched", "serve"],
+                    help="hss: the HSS n=65536 headline; exp: the exponential-kernel HODLR n=262144; "
+                         "hodlr4096: HODLR n=4096 FP64 r=1; batched: 512 uneven matrices; serve: Poisson requests")
+    ap.add_argument("--storages", default="", help="exp: comma-separated storages (default all)")
+    ap.add_argument("--rhs", default="", help="exp: comma-separated right-hand-side counts (default 1,128)")
     ap.add_argument("--count", type=int, default=0, help="matrices in the batched / serving workload")
     ap.add_argument("--rates", default="1000,5000,10000,20000,50000")
     ap.add_argument("--seconds", type=float, default=1.0, help="arrival window per rate (serve)")
@@ -755,16 +758,25 @@ def run_serve(args):
     return 0
 
 
-def run_workloads(hm, torch, np, peaks, pipes, steps, warmup, with_cpu):
+def run_workloads(hm, torch, np, peaks, pipes, steps, warmup, with_cpu, which=("hodlr4096", "exp"), storages=None,
+                  rhs=None):
     """The other single-matrix workloads, each with its own roofline:
     HODLR n=4096 leaf 128 rank 8 r=1 FP64 (L2-resident: 48 rotating copies)
     and the exact rank-8 exponential kernel HODLR n=262144 leaf 256 at r=1 and
     r=128 in every storage; errors against the oracle (the O(nK) recurrence
     for r=1, sampled dense rows for r=128, the dense product for n=4096)."""
-    import workloads as W
-    from oracle import expkernel as OE, matmat as OM
     out = {}
-    # HODLR n=4096, FP64, r=1
+    if "hodlr4096" in which:
+        out.update(_run_hodlr4096(hm, torch, np, peaks, pipes, steps, warmup, with_cpu))
+    if "exp" in which:
+        out.update(_run_exp(hm, torch, np, peaks, pipes, steps, warmup, with_cpu, storages, rhs))
+    return out
+
+
+def _run_hodlr4096(hm, torch, np, peaks, pipes, steps, warmup, with_cpu):
+    import workloads as W
+    from oracle import matmat as OM
+    out = {}
     rng = W.rng_named("hodlr_n4096_m128_k8_r1_f64")
     tree = hm.Tree.default(4096, 128)
     c = tree.leaf_ends
@@ -779,7 +791,13 @@ def run_workloads(hm, torch, np, peaks, pipes, steps, warmup, with_cpu):
     if with_cpu:
         ent["err_vs_oracle"] = col_err(Y, OM.matmat(c, g, X))
     out["hodlr_n4096_r1_f64"] = ent
-    # exponential kernel, n=262144
+    return out
+
+
+def _run_exp(hm, torch, np, peaks, pipes, steps, warmup, with_cpu, storages=None, rhs=None):
+    import workloads as W
+    from oracle import expkernel as OE, matmat as OM
+    out = {}
     rng = W.rng_named("hodlr_exp_n262144_m256_K8")
     n = 262144
     t = W.exp_points(rng, n)
@@ -788,10 +806,13 @@ def run_workloads(hm, torch, np, peaks, pipes, steps, warmup, with_cpu):
     c = tree.leaf_ends
     g = W.exp_kernel_hodlr(t, c, ck, lk)
     rows = sorted(set([0, n - 1] + [int(v) for v in np.linspace(255, n - 2, 158)]))
-    for r, storages in ((1, ("f32", "bf16", "bf16x2", "f64")), (128, ("bf16", "bf16x2", "f32", "f64"))):
+    for r, sts in ((1, ("f32", "bf16", "bf16x2", "f64")), (128, ("bf16", "bf16x2", "f32", "f64"))):
         X = rng.standard_normal((n, r))
-        ref = None
-        for st in storages:
+        if rhs and r not in rhs:
+            continue
+        for st in sts:
+            if storages and st not in storages:
+                continue
             w, _ = phase_work(g, n, r, st)
             f64_split = st == "f64" and r >= 12
             if f64_split:
@@ -819,6 +840,23 @@ def run_workloads(hm, torch, np, peaks, pipes, steps, warmup, with_cpu):
     return out
 
 
+def run_workload_only(args):
+    """One of the other single-matrix workloads on its own (one JSON line)."""
+    import numpy as np
+    import torch
+    import paper_1909_07909_gb300 as hm
+    torch.cuda.set_device(0)
+    peaks, _ = measured_peaks()
+    pipes = probe_pipes()
+    storages = [v for v in args.storages.split(",") if v] or None
+    rhs = [int(v) for v in args.rhs.split(",") if v] or None
+    res = run_workloads(hm, torch, np, peaks, pipes, args.steps, args.warmup, not args.no_cpu, (args.workload,),
+                        storages, rhs)
+    print(json.dumps({"metric": METRIC, "workload": args.workload, "unit": "GB/s", "data": "synthetic",
+                      "variants": res, "pipe_probe": pipes}))
+    return 0
+
+
 def main():
     args = parse()
     rank, local, world = dist_env()
@@ -826,6 +864,8 @@ def main():
         return run_reference(args)
     if args.probe_sweep:
         return probe_sweep() if rank == 0 else 0
+    if args.workload in ("exp", "hodlr4096"):
+        return run_workload_only(args) if rank == 0 else 0
     if args.workload == "batched":
         return run_batched(args) if rank == 0 else 0
     if args.workload == "serve":

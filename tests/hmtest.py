@@ -44,6 +44,28 @@ def col_rel_err(Y, ref):
     return float(np.max(num / den)) if ref.size else 0.0
 
 
+# Normwise gate per column for the BF16 storages: ||y - y_oracle||_2 / ||y_oracle||_2
+# <= 8 u_s.  The componentwise bound alone is c_round u_s times an envelope
+# that can be several times |y|, loose enough to pass a dropped level.
+NORMWISE = {"bf16": 8 * 2.0 ** -9, "bf16x2": 8 * 2.0 ** -17}
+
+
+class Bound(float):
+    """A componentwise bound factor that remembers the storage type it was
+    derived for, so that check_bound also applies that storage's normwise gate
+    (sums with plain numbers keep the storage)."""
+
+    def __new__(cls, value, storage):
+        obj = float.__new__(cls, value)
+        obj.storage = storage
+        return obj
+
+    def __add__(self, other):
+        return Bound(float(self) + float(other), self.storage)
+
+    __radd__ = __add__
+
+
 def bound_factor(storage, kind, p, acc_len, tensor_core=False):
     """(c_round * u_s + gamma_L(u_acc)): rounded factors on the longest product chain
     (HODLR: U, V, X and the staged T; HSS: U, V, X, y-hat and the 2(p-1) translations
@@ -57,7 +79,7 @@ def bound_factor(storage, kind, p, acc_len, tensor_core=False):
         c_round += 2   # intermediates (T / x-hat / y-hat) held in float32
     if storage in ("bf16", "bf16x2"):
         c_round += 2   # the tensor-core path rounds X and Z to the storage format
-    return c_round * u_s + OB.gamma(acc_len, u_acc)
+    return Bound(c_round * u_s + OB.gamma(acc_len, u_acc), storage)
 
 
 def acc_length(info, kind):
@@ -67,8 +89,12 @@ def acc_length(info, kind):
 
 def check_bound(Y, ref, env, factor, what=""):
     err = np.abs(np.asarray(Y, dtype=np.float64).reshape(ref.shape) - ref)
-    tol = factor * env + 1e-300
+    tol = float(factor) * env + 1e-300
     bad = err > tol
     ratio = float(np.max(err / tol)) if ref.size else 0.0
     assert not bad.any(), "%s: %d entries beyond the bound; max err/bound = %.3g" % (what, int(bad.sum()), ratio)
+    gate = NORMWISE.get(getattr(factor, "storage", None))
+    if gate is not None and ref.size:
+        nw = col_rel_err(Y, ref)
+        assert nw <= gate, "%s: normwise per-column error %.3g above %.3g" % (what, nw, gate)
     return ratio
