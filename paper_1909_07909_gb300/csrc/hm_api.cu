@@ -288,15 +288,9 @@ static hm_status upload(const void* h, size_t bytes, void** d, size_t* total) {
 static void free_matrix_device(hm_matrix* A) {
   void* ptrs[] = {A->d_off, A->d_A, A->d_A_lo, A->d_W, A->d_W_lo, A->d_RU, A->d_RVt, A->d_B12,
                   A->d_B21, A->d_ws, A->d_cnt, A->d_io};
-  if (A->side) cudaStreamSynchronize(A->side);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   A->d_off = nullptr;
-  if (A->ev_fork) cudaEventDestroy(A->ev_fork);
-  if (A->ev_join) cudaEventDestroy(A->ev_join);
-  if (A->side) cudaStreamDestroy(A->side);
-  A->ev_fork = A->ev_join = nullptr;
-  A->side = nullptr;
 }
 
 }  // namespace hmi
@@ -642,23 +636,6 @@ size_t tree_counter_count(const MatView& mv, int64_t r) {
 size_t counter_count(const MatView& mv, int64_t r) { return tree_counter_count(mv, r) + 8; }
 
 hm_status ensure_scratch(hm_matrix* A, int64_t r) {
-  if (A->storage == HM_F64 && !A->side && r >= kF64TiledMinR) {
-    // FP64 products fork their diagonal-block product onto a second stream
-    int dev_prev = -1;
-    cudaGetDevice(&dev_prev);
-    if (dev_prev != A->device) cudaSetDevice(A->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&A->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A->ev_join, cudaEventDisableTiming);
-    if (dev_prev != A->device) cudaSetDevice(dev_prev);
-    if (e != cudaSuccess) {
-      if (A->ev_fork) cudaEventDestroy(A->ev_fork);
-      if (A->side) cudaStreamDestroy(A->side);
-      A->side = nullptr;
-      A->ev_fork = A->ev_join = nullptr;
-      return cuda_fail(e, "FP64 side stream");
-    }
-  }
   if (r <= A->r_cap && A->d_ws) return HM_OK;
   const MatView mv = A->view();
   const size_t cs = (A->storage == HM_F64) ? 8 : 4;
@@ -786,42 +763,6 @@ hm_status launch_product(hm_matrix* A, const MatView& mv, const Scratch& ws, int
       default: return simt_phase_bf16x2(ph, mv, ws, r, X, ldx, xt, Y, ldy, yt, s, pdl);
     }
   };
-  if (f64_tiled(mv, r) && A->side && !ws.prof) {
-    // FP64, wide blocks, every phase bound by the FP64 pipe (k_f64.cu): the
-    // diagonal-block product D X, which needs nothing from the tree, runs on
-    // the side stream (one persistent block per SM) while the projection and
-    // the tree run here; the expansion Y += E Z joins both.  Profiled
-    // products take the sequential path below so that every kernel is timed
-    // on its own.
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaEventRecord(A->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(A->side, A->ev_fork, 0);
-    if (e != cudaSuccess) {
-      set_error("FP64 fork: %s", cudaGetErrorString(e));
-      return HM_ECUDA;
-    }
-    hm_status st = f64_leaf_phase(1, mv, ws, r, X, ldx, Y, ldy, A->side, false, sms);
-    // the join is recorded whatever happened, so `s` never runs ahead of the side stream
-    e = cudaEventRecord(A->ev_join, A->side);
-    if (st == HM_OK) st = f64_leaf_phase(0, mv, ws, r, X, ldx, Y, ldy, s, false, 0);
-    if (st == HM_OK) {
-      st = launch_tree_cluster(A, mv, ws, r, s, true);
-      A->tree_last_cluster = (st == HM_OK);
-      if (st == HM_EUNSUPPORTED) {
-        st = phase(1, true);
-        if (st == HM_OK) st = phase(2, true);
-      }
-    }
-    const cudaError_t e2 = (e == cudaSuccess) ? cudaStreamWaitEvent(s, A->ev_join, 0) : e;
-    if (st != HM_OK) return st;
-    if (e2 != cudaSuccess) {
-      set_error("FP64 join: %s", cudaGetErrorString(e2));
-      return HM_ECUDA;
-    }
-    return f64_leaf_phase(2, mv, ws, r, X, ldx, Y, ldy, s, false, 0);
-  }
   if (f64_tiled(mv, r)) {
     // FP64, wide blocks, one stream: projection -> tree -> D X (programmatic
     // launch: it may start beside the tree) -> Y += E Z

@@ -84,9 +84,6 @@ struct hm_matrix {
   int tree_ns = 0;              //   operator ring slots
   bool tree_last_cluster = false;  // the last product ran the cluster tree kernel
   hmi::Prof* prof = nullptr;   // set while profiling is enabled
-  cudaStream_t side = nullptr;   // FP64: stream of the diagonal-block product, forked from
-  cudaEvent_t ev_fork = nullptr; //   and joined back to the product's stream (created with
-  cudaEvent_t ev_join = nullptr; //   the scratch; the no-allocation entry point only reuses them)
   CUtensorMap tmA;              // TMA descriptors of the expansion planes (BF16 / BF16X2)
   CUtensorMap tmAlo;
   CUtensorMap tmW;              // ... and of the projection planes

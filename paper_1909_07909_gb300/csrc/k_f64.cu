@@ -14,10 +14,9 @@
 //    an atomic counter, so the last wave does not leave SMs idle;
 //  * the diagonal-block product D_i X_i, three quarters of the work, is its
 //    own launch right after the tree kernel, with programmatic dependent
-//    launch: it needs nothing from the tree, so its blocks start on the room
-//    the tree leaves on the SMs (34 KB of shared memory each) and fill the
-//    FP64 pipes while the tree's dependent level chain runs.  It waits for the
-//    tree (griddepcontrol.wait) only before it exits, so that its completion
+//    launch: it needs nothing from the tree, so it may start as soon as the
+//    tree's blocks are resident and room frees up.  It waits for the tree
+//    (griddepcontrol.wait) only before it exits, so that its completion
 //    implies the tree's; the expansion E_i Z_i, launched after it, then adds
 //    to its result.
 //

@@ -50,31 +50,6 @@ __device__ __forceinline__ uint4 ld_stream16(const void* p) {
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-// V consecutive elements of a generator plane, starting at element `elem`.
-template <int S>
-__device__ __forceinline__ void load_vec(const void* A, const void* A_lo, int64_t elem,
-                                         typename Stor<S>::C* a) {
-  if constexpr (S == HM_F64) {
-    const uint4 u = ld_stream16(static_cast<const double*>(A) + elem);
-    a[0] = __hiloint2double(static_cast<int>(u.y), static_cast<int>(u.x));
-    a[1] = __hiloint2double(static_cast<int>(u.w), static_cast<int>(u.z));
-  } else if constexpr (S == HM_F32) {
-    const uint4 u = ld_stream16(static_cast<const float*>(A) + elem);
-    a[0] = __uint_as_float(u.x); a[1] = __uint_as_float(u.y);
-    a[2] = __uint_as_float(u.z); a[3] = __uint_as_float(u.w);
-  } else {
-    const uint4 u = ld_stream16(static_cast<const uint16_t*>(A) + elem);
-    a[0] = bf_lo(u.x); a[1] = bf_hi(u.x); a[2] = bf_lo(u.y); a[3] = bf_hi(u.y);
-    a[4] = bf_lo(u.z); a[5] = bf_hi(u.z); a[6] = bf_lo(u.w); a[7] = bf_hi(u.w);
-    if constexpr (S == HM_BF16X2) {
-      // hi + lo is exact in float (at most 17 significant bits).
-      const uint4 w = ld_stream16(static_cast<const uint16_t*>(A_lo) + elem);
-      a[0] += bf_lo(w.x); a[1] += bf_hi(w.x); a[2] += bf_lo(w.y); a[3] += bf_hi(w.y);
-      a[4] += bf_lo(w.z); a[5] += bf_hi(w.z); a[6] += bf_lo(w.w); a[7] += bf_hi(w.w);
-    }
-  }
-}
-
 // V consecutive compute-type values from shared memory (16-byte aligned).
 template <typename C, int V>
 __device__ __forceinline__ void load_b(const C* p, C* b) {
@@ -249,8 +224,33 @@ __device__ __forceinline__ int rs_index(int lane, int i) {
   return idx;
 }
 
+// The V values of one raw 16-byte vector of a generator plane (hi plane, and
+// for BF16X2 the lo plane: hi + lo is exact in float, at most 17 bits).
+template <int S>
+__device__ __forceinline__ void unpack_vec(const uint4& u, const uint4& w, typename Stor<S>::C* a) {
+  if constexpr (S == HM_F64) {
+    a[0] = __hiloint2double(static_cast<int>(u.y), static_cast<int>(u.x));
+    a[1] = __hiloint2double(static_cast<int>(u.w), static_cast<int>(u.z));
+  } else if constexpr (S == HM_F32) {
+    a[0] = __uint_as_float(u.x); a[1] = __uint_as_float(u.y);
+    a[2] = __uint_as_float(u.z); a[3] = __uint_as_float(u.w);
+  } else {
+    a[0] = bf_lo(u.x); a[1] = bf_hi(u.x); a[2] = bf_lo(u.y); a[3] = bf_hi(u.y);
+    a[4] = bf_lo(u.z); a[5] = bf_hi(u.z); a[6] = bf_lo(u.w); a[7] = bf_hi(u.w);
+    if constexpr (S == HM_BF16X2) {
+      a[0] += bf_lo(w.x); a[1] += bf_hi(w.x); a[2] += bf_lo(w.y); a[3] += bf_hi(w.y);
+      a[4] += bf_lo(w.z); a[5] += bf_hi(w.z); a[6] += bf_lo(w.w); a[7] += bf_hi(w.w);
+    }
+  }
+}
+
 // Os[c * OS + t] = sum_k A(row0 + t, k) * Bs[c * KS + k] for t < nrows, c < RC.
 // A: row-major plane(s) with leading dimension lda (elements), K a multiple of V.
+// Lane l sums the 16-byte vectors q = l, l + 32, ... of each of its warp's TR
+// rows in increasing q, then a butterfly over the lanes completes each sum;
+// the order does not depend on TR, so every TR gives the same bits.  All
+// loads of two q steps of the TR rows are issued (as raw vectors) before the
+// multiplies, so a narrow right-hand side keeps 2 TR loads in flight per lane.
 template <int S, int RC, int TR>
 __device__ __forceinline__ void rows_gemm(const void* A, const void* A_lo, int64_t row0, int64_t lda,
                                           int nrows, int K, const typename Stor<S>::C* Bs, int KS,
@@ -260,34 +260,49 @@ __device__ __forceinline__ void rows_gemm(const void* A, const void* A_lo, int64
   constexpr int T = TR * RC;
   constexpr int NV = (T >= 32) ? T / 32 : 1;
   constexpr int OWN = (T >= 32) ? 0 : (32 / T - 1);
+  constexpr int ES = (S == HM_F64) ? 8 : (S == HM_F32) ? 4 : 2;   // bytes per element of a plane
+  constexpr bool LO = (S == HM_BF16X2);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int Q = K / V;
+  const unsigned char* Ab = static_cast<const unsigned char*>(A);
+  const unsigned char* Lb = static_cast<const unsigned char*>(A_lo);
   for (int t0 = warp * TR; t0 < nrows; t0 += nw * TR) {
     C acc[T];
 #pragma unroll
     for (int i = 0; i < T; ++i) acc[i] = C(0);
-#pragma unroll 2
-    for (int q = lane; q < Q; q += 32) {
-      C a[TR][V];
+    for (int q0 = lane; q0 < Q; q0 += 64) {
+      uint4 ra[2][TR], rl[2][TR];
 #pragma unroll
-      for (int t = 0; t < TR; ++t) {
-        if (t0 + t < nrows) {
-          load_vec<S>(A, A_lo, (row0 + t0 + t) * lda + static_cast<int64_t>(q) * V, a[t]);
-        } else {
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + 32 * u;
 #pragma unroll
-          for (int v = 0; v < V; ++v) a[t][v] = C(0);
+        for (int t = 0; t < TR; ++t) {
+          ra[u][t] = make_uint4(0u, 0u, 0u, 0u);
+          rl[u][t] = make_uint4(0u, 0u, 0u, 0u);
+          if (q < Q && t0 + t < nrows) {
+            const int64_t off = ((row0 + t0 + t) * lda + static_cast<int64_t>(q) * V) * ES;
+            ra[u][t] = ld_stream16(Ab + off);
+            if constexpr (LO) rl[u][t] = ld_stream16(Lb + off);
+          }
         }
       }
 #pragma unroll
-      for (int c = 0; c < RC; ++c) {
-        C b[V];
-        load_b<C, V>(Bs + c * KS + q * V, b);
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + 32 * u;
+        if (q >= Q) break;
 #pragma unroll
-        for (int t = 0; t < TR; ++t) {
+        for (int c = 0; c < RC; ++c) {
+          C b[V];
+          load_b<C, V>(Bs + c * KS + q * V, b);
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[t * RC + c] = fma(a[t][v], b[v], acc[t * RC + c]);
+          for (int t = 0; t < TR; ++t) {
+            C a[V];
+            unpack_vec<S>(ra[u][t], rl[u][t], a);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[t * RC + c] = fma(a[v], b[v], acc[t * RC + c]);
+          }
         }
       }
     }
@@ -927,9 +942,10 @@ hm_status simt_phase_t(int phase, const MatView& mv, const Scratch& ws, int64_t 
       default: HM_PHASE(32, 1);
     }
   }
+  constexpr int TRN = (S == HM_F32 || S == HM_BF16) ? 8 : 4;   // rows per warp pass, narrow right-hand sides
   switch (rc) {
-    case 1: HM_PHASE(1, 4);
-    case 2: HM_PHASE(2, 4);
+    case 1: HM_PHASE(1, TRN);
+    case 2: HM_PHASE(2, TRN);
     case 4: HM_PHASE(4, 4);
     case 8: HM_PHASE(8, 4);
     case 16: HM_PHASE(16, (dbl ? 2 : 4));
