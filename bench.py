@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="skip the n=4096 and n=262144 workloads")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the HSS solve variant")
     ap.add_argument("--cpu-leaves", type=int, default=6, help="leaf row blocks in the CPU oracle sample")
     ap.add_argument("--workload", default="hss", choices=["hss", "exp", "hodlr4096", "batched", "serve"],
                     help="hss: the HSS n=65536 headline; exp: the exponential-kernel HODLR n=262144; "
@@ -408,6 +409,35 @@ def e2e_host(hm, torch, tree, g, storage, X, steps, copies):
     return {"value": b / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n * r * xs,
             "d2h_bytes_per_step": n * r * ys, "ms_per_step": dt * 1e3,
             "l2": "%d rotating resident matrices" % copies}
+
+
+def time_ulv(hm, torch, tree, g, X, steps):
+    """The HSS solve X = A^{-1} B (Sec. 4.3, implicit ULV) on the headline
+    matrix in FP64: the factorization once (host-timed, synchronous), then
+    `steps` solves with the 64 right-hand sides (CUDA events), and the backward
+    error ||A X - B||_F / ||B||_F through the FP64 product."""
+    A = hm.Matrix.create(tree, g, "f64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F = A.ulv()
+    t_factor = time.perf_counter() - t0
+    n, r = X.shape
+    B = torch.from_numpy(X.T.copy()).cuda().t()
+    Xs = F.solve(B)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        F.solve(B, Xs)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    R = A.matmat(Xs) - B
+    rel = (torch.linalg.norm(R) / torch.linalg.norm(B)).item()
+    F.close()
+    return {"storage": "f64", "rhs": r, "factor_ms": t_factor * 1e3, "ms_per_solve": ms, "steps": steps,
+            "backward_error": rel, "metric": "||A X - B||_F / ||B||_F through the FP64 product"}
 
 
 def cpu_fast_baseline(c, g, X, runs=3):
@@ -966,6 +996,8 @@ def main():
                                     "storage": "bf16", "ranks": "8 o 4 = 32", "generator_bytes": r_["generator_bytes"],
                                     "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
                                                           for k in range(len(PHASES))}}
+        if not args.no_variants and not args.no_solve:
+            variants["ulv_solve_f64"] = time_ulv(hm, torch, tree, g, X, max(5, min(20, args.steps)))
         if not args.no_workloads:
             variants.update(run_workloads(hm, torch, np, peaks, pipes, args.steps, 3, not args.no_cpu and world == 1))
         if not args.no_cpu and world == 1:

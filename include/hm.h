@@ -56,6 +56,7 @@ typedef struct hm_tree hm_tree;
 typedef struct hm_matrix hm_matrix;
 typedef struct hm_batch hm_batch;
 typedef struct hm_server hm_server;
+typedef struct hm_ulv hm_ulv;
 
 /* Static description of a status code; never NULL. */
 const char* hm_status_string(hm_status s);
@@ -344,6 +345,38 @@ hm_status hm_matrix_profile(hm_matrix* A, int32_t enable);
 hm_status hm_matrix_phase_times(hm_matrix* A, double ms[5], int64_t launches[5]);
 
 /* ---------------------------------------------------------------------- */
+/* Solves with an HSS matrix (Sec. 4.3)                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Factors an HSS matrix A (F64 storage) for solves by the implicit ULV
+ * scheme of Sec. 4.3, on A's device.  Level by level from the leaves: a QL
+ * factorization of each node's row basis (Q^T U = [0; Ut], Step 1), an LQ of
+ * the top rows of Q^T D that triangularizes them (Z, Step 1), the split of
+ * the product into a block-triangular factor and a reduced system on the
+ * trailing ku x ku blocks (Step 2), and the merge of sibling nodes into the
+ * next level's blocks (Step 3); the root's block gets a full LQ.  Kept per
+ * node on the device: Q^T and Z (n x n), the inverse of the triangular block,
+ * the blocks that carry solved parts across levels.  Memory: about three
+ * times the dense leaf blocks (leaves padded with identity rows to at least
+ * ku + 1).  The reflectors are chosen without pivoting, as in the paper; a
+ * singular A (or one whose eliminated blocks are singular) gives infinities.
+ * Requires equal padded row and column ranks and depth >= 1 (HM_EUNSUPPORTED
+ * otherwise).  A must outlive the factorization (its translation operators
+ * are read by hm_ulv_solve).  Synchronous.
+ * Errors: HM_EINVAL (NULL out, not an HSS matrix, wrong device),
+ * HM_EUNSUPPORTED, HM_ENOMEM, HM_ECUDA.  *out is NULL on any error. */
+hm_status hm_ulv_factor(const hm_matrix* A, hm_ulv** out);
+
+/* X = A^{-1} B with the factorization F: B and X are n x r float64 device
+ * buffers, column-major with leading dimensions ldb, ldx >= n; they may be
+ * the same buffer only if ldb = ldx.  Applies Q^T, the triangular solves and
+ * the merges upward, the root's solve, then Z downward (Step 4): a sequence
+ * of batched FP64 products queued on `stream`.  The first call with a given
+ * r allocates the work space (and synchronises); calls on one factorization
+ * must not run concurrently. */
+hm_status hm_ulv_solve(const hm_ulv* F, int64_t r, const void* B, int64_t ldb, void* X, int64_t ldx, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Batched products (the paper runs one product at a time; batching many   */
 /* matrices is this library's addition)                                    */
 /* ---------------------------------------------------------------------- */
@@ -457,7 +490,8 @@ hm_status hm_serve_pause(hm_server* s, int32_t pause);
 hm_status hm_serve_stats(hm_server* s, hm_serve_stats_t* out);
 hm_status hm_serve_reset_stats(hm_server* s);
 
-/* Releases any object created by this library (tree, matrix, batch, server).
+/* Releases any object created by this library (tree, matrix, batch, server,
+ * ULV factorization).
  * NULL-safe.  A matrix registered with a server must be released after the
  * server. */
 void hm_destroy(void* any);

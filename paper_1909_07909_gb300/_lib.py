@@ -110,6 +110,8 @@ _decl("hm_set_device_wait_limit", C.c_int, C.c_uint64)
 _decl("hm_get_device_wait_limit", C.c_int, C.POINTER(C.c_uint64))
 _decl("hm_selftest_device_timeout", C.c_int, vp)
 _decl("hm_inject_alloc_failures", C.c_int, C.c_int32)
+_decl("hm_ulv_factor", C.c_int, vp, C.POINTER(vp))
+_decl("hm_ulv_solve", C.c_int, vp, C.c_int64, vp, C.c_int64, vp, C.c_int64, vp)
 _decl("hm_destroy", None, vp)
 
 

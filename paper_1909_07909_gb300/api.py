@@ -177,6 +177,12 @@ class Matrix:
         check(lib.hm_hadamard(self._h, other._h, C.byref(h)), "hm_hadamard")
         return Matrix(h, self.kind, self.tree)
 
+    def ulv(self):
+        """Implicit ULV factorization of this HSS matrix (Sec. 4.3) for solves."""
+        h = vp()
+        check(lib.hm_ulv_factor(self._h, C.byref(h)), "hm_ulv_factor")
+        return Ulv(h, self)
+
     def reserve(self, r_max):
         check(lib.hm_matrix_reserve(self._h, int(r_max)), "hm_matrix_reserve")
 
@@ -287,6 +293,36 @@ class Batch:
         if h:
             lib.hm_destroy(h)
             self._h = None
+
+
+class Ulv:
+    """A factorization for solves X = A^{-1} B (keeps its matrix alive)."""
+
+    def __init__(self, handle, matrix):
+        self._h = handle
+        self.matrix = matrix
+
+    def solve(self, B, X=None, stream=None):
+        """X = A^{-1} B for an (n, r) float64 column-major device tensor B."""
+        n = self.matrix.tree.shape()[0]
+        if B.dim() == 1:
+            B = B.reshape(-1, 1)
+        r = B.shape[1]
+        if X is None:
+            X = torch.empty((r, n), dtype=torch.float64, device=B.device).t()
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        check(lib.hm_ulv_solve(self._h, int(r), vp(B.data_ptr()), int(B.stride(1)) if r > 1 else n,
+                               vp(X.data_ptr()), int(X.stride(1)) if r > 1 else n, vp(st)), "hm_ulv_solve")
+        return X
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.hm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class Server:

@@ -145,5 +145,7 @@ hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, i
 // Releases batch and server objects (defined with them).
 void destroy_other(void* any, uint32_t magic);
 void destroy_server(void* any);
+void destroy_ulv(void* any);
+bool is_ulv(const void* any);
 
 }  // namespace hmi

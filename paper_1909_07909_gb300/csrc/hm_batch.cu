@@ -534,6 +534,7 @@ namespace hmi {
 void destroy_other(void* any, uint32_t magic) {
   if (magic == kMagicBatch) destroy_batch(static_cast<hm_batch*>(any));
   else if (magic == kMagicServer) destroy_server(any);
+  else if (is_ulv(any)) destroy_ulv(any);
 }
 
 }  // namespace hmi

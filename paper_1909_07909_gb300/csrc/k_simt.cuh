@@ -942,7 +942,7 @@ hm_status simt_phase_t(int phase, const MatView& mv, const Scratch& ws, int64_t 
       default: HM_PHASE(32, 1);
     }
   }
-  constexpr int TRN = (S == HM_F32 || S == HM_BF16) ? 8 : 4;   // rows per warp pass, narrow right-hand sides
+  constexpr int TRN = 4;   // rows per warp pass, narrow right-hand sides (8 measured slower: 120+ registers)
   switch (rc) {
     case 1: HM_PHASE(1, TRN);
     case 2: HM_PHASE(2, TRN);
