@@ -248,10 +248,11 @@ __device__ __forceinline__ void unpack_vec(const uint4& u, const uint4& w, typen
 // A: row-major plane(s) with leading dimension lda (elements), K a multiple of V.
 // Lane l sums the 16-byte vectors q = l, l + 32, ... of each of its warp's TR
 // rows in increasing q, then a butterfly over the lanes completes each sum;
-// the order does not depend on TR, so every TR gives the same bits.  All
-// loads of two q steps of the TR rows are issued (as raw vectors) before the
-// multiplies, so a narrow right-hand side keeps 2 TR loads in flight per lane.
-template <int S, int RC, int TR>
+// the order does not depend on TR or UQ, so every shape gives the same bits.
+// All loads of UQ q steps of the TR rows are issued (as raw vectors) before
+// the multiplies, so a narrow right-hand side keeps UQ TR loads in flight per
+// lane.
+template <int S, int RC, int TR, int UQ = 2>
 __device__ __forceinline__ void rows_gemm(const void* A, const void* A_lo, int64_t row0, int64_t lda,
                                           int nrows, int K, const typename Stor<S>::C* Bs, int KS,
                                           typename Stor<S>::C* Os, int OS) {
@@ -272,10 +273,10 @@ __device__ __forceinline__ void rows_gemm(const void* A, const void* A_lo, int64
     C acc[T];
 #pragma unroll
     for (int i = 0; i < T; ++i) acc[i] = C(0);
-    for (int q0 = lane; q0 < Q; q0 += 64) {
-      uint4 ra[2][TR], rl[2][TR];
+    for (int q0 = lane; q0 < Q; q0 += 32 * UQ) {
+      uint4 ra[UQ][TR], rl[UQ][TR];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UQ; ++u) {
         const int q = q0 + 32 * u;
 #pragma unroll
         for (int t = 0; t < TR; ++t) {
@@ -289,7 +290,7 @@ __device__ __forceinline__ void rows_gemm(const void* A, const void* A_lo, int64
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UQ; ++u) {
         const int q = q0 + 32 * u;
         if (q >= Q) break;
 #pragma unroll
@@ -745,7 +746,7 @@ __device__ __forceinline__ C z_value(const MatView& mv, const Scratch& ws, int64
   return C(0);
 }
 
-template <int S, int RC, int TR>
+template <int S, int RC, int TR, int UQ = 2>
 __device__ void expand_block(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx, int xt,
                              void* Y, int64_t ldy, int yt, int RT, int leaf, int tile, int chunk,
                              typename Stor<S>::C* sm) {
@@ -770,7 +771,7 @@ __device__ void expand_block(const MatView& mv, const Scratch& ws, int64_t r, co
     Bs[c * K + mp + e] = (c < ncols) ? z_value<C>(mv, ws, r, leaf, e, col0 + c) : C(0);
   }
   __syncthreads();
-  rows_gemm<S, RC, TR>(mv.A, mv.A_lo, a0 + t0, mv.We, nrows, K, Bs, K, Os, OS);
+  rows_gemm<S, RC, TR, UQ>(mv.A, mv.A_lo, a0 + t0, mv.We, nrows, K, Bs, K, Os, OS);
   __syncthreads();
   for (int idx = threadIdx.x; idx < ncols * nrows; idx += blockDim.x) {
     const int c = idx / nrows, t = idx % nrows;
@@ -778,13 +779,13 @@ __device__ void expand_block(const MatView& mv, const Scratch& ws, int64_t r, co
   }
 }
 
-template <int S, int RC, int TR>
+template <int S, int RC, int TR, int UQ = 2>
 __global__ void __launch_bounds__(256) k_expand(MatView mv, Scratch ws, int64_t r, const void* X,
                                                 int64_t ldx, int xt, void* Y, int64_t ldy, int yt,
                                                 int RT, int tiles_per_leaf) {
   using C = typename Stor<S>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  expand_block<S, RC, TR>(mv, ws, r, X, ldx, xt, Y, ldy, yt, RT, blockIdx.x / tiles_per_leaf,
+  expand_block<S, RC, TR, UQ>(mv, ws, r, X, ldx, xt, Y, ldy, yt, RT, blockIdx.x / tiles_per_leaf,
                           blockIdx.x % tiles_per_leaf, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
@@ -825,7 +826,7 @@ inline int down_depth(const MatView& mv, size_t esz) {
   return std::min(d, mv.p - 1);
 }
 
-template <int S, int RC, int TR>
+template <int S, int RC, int TR, int UQ = 2>
 hm_status launch_phase_rc(int phase, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                           int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
   using C = typename Stor<S>::C;
@@ -856,9 +857,9 @@ hm_status launch_phase_rc(int phase, const MatView& mv, const Scratch& ws, int64
     const int tiles = (mv.m_pad + RT - 1) / RT;
     const size_t smem = sizeof(C) * static_cast<size_t>(RC * mv.We + RC * (RT + 1));
     if (smem > 220 * 1024) return HM_EUNSUPPORTED;
-    cudaFuncSetAttribute(k_expand<S, RC, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaFuncSetAttribute(k_expand<S, RC, TR, UQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     prof_mark(ws.prof, 3, true, st);
-    e = launch_k(k_expand<S, RC, TR>, dim3(mv.L * tiles, nchunks), dim3(256), smem, st, pdl, mv, wk, r, X, ldx,
+    e = launch_k(k_expand<S, RC, TR, UQ>, dim3(mv.L * tiles, nchunks), dim3(256), smem, st, pdl, mv, wk, r, X, ldx,
                  xt, Y, ldy, yt, RT, tiles);
     prof_mark(ws.prof, 3, false, st);
   }
@@ -932,6 +933,8 @@ hm_status simt_phase_t(int phase, const MatView& mv, const Scratch& ws, int64_t 
   const int width = (phase == 3) ? mv.We : mv.m_pad;
   const int rc = pick_rc(r, esz, width);
 #define HM_PHASE(RC_, TR_) return launch_phase_rc<S, RC_, TR_>(phase, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl)
+#define HM_PHASE_U(RC_, TR_, UQ_) \
+  return launch_phase_rc<S, RC_, TR_, UQ_>(phase, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl)
   if (phase == 0) {           // few rows (Kp) per block: one row per warp pass
     switch (rc) {
       case 1: HM_PHASE(1, 2);
@@ -942,16 +945,21 @@ hm_status simt_phase_t(int phase, const MatView& mv, const Scratch& ws, int64_t 
       default: HM_PHASE(32, 1);
     }
   }
-  constexpr int TRN = 4;   // rows per warp pass, narrow right-hand sides (8 measured slower: 120+ registers)
+  // Narrow right-hand sides: 4 rows and two q steps per warp pass; BF16 rows
+  // are short (a 672-byte row is 42 vectors, so the second q step would keep
+  // 10 lanes busy), so BF16 takes 8 rows and one q step (same registers)
+  constexpr int TRN = (S == HM_BF16) ? 8 : 4;
+  constexpr int UQN = (S == HM_BF16) ? 1 : 2;
   switch (rc) {
-    case 1: HM_PHASE(1, TRN);
-    case 2: HM_PHASE(2, TRN);
+    case 1: HM_PHASE_U(1, TRN, UQN);
+    case 2: HM_PHASE_U(2, TRN, UQN);
     case 4: HM_PHASE(4, 4);
     case 8: HM_PHASE(8, 4);
     case 16: HM_PHASE(16, (dbl ? 2 : 4));
     default: HM_PHASE(32, (dbl ? 1 : 2));
   }
 #undef HM_PHASE
+#undef HM_PHASE_U
 }
 
 }  // namespace hmi
