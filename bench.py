@@ -320,8 +320,10 @@ def time_variant(hm, torch, tree, g, storage, X, steps, warmup, copies, clock_in
     Xh = torch.from_numpy(X.T.copy())
     Xs = [Xh.to(dev).to(xd).t() for _ in range(copies)]
     Ys = [torch.empty((r, n), dtype=td, device=dev).t() for _ in range(copies)]
+    tree_ms = None
     for A in mats:
         A.reserve(r)
+        tree_ms = A.tune_tree(r)   # the fastest launch shape of the tree kernel (no result changes)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     code = hm.HM_F64 if storage == "f64" else hm.HM_F32
@@ -371,7 +373,9 @@ def time_variant(hm, torch, tree, g, storage, X, steps, warmup, copies, clock_in
            "phases": {"ms": acc_ms, "launches": acc_n, "steps": ps},
            "clocks": sampler.summary() if sampler else None,
            "generator_bytes": mats[0].generator_bytes(), "info": info,
-           "launches_per_step": sum(acc_n) / ps}
+           "launches_per_step": sum(acc_n) / ps,
+           "tree_shape": {"cluster_ctas": info["tree_cluster"], "columns": info["tree_columns"],
+                          "ring_slots": info["tree_ring"], "tuned_ms": tree_ms}}
     res["gbs"] = res["bytes_per_step"] / (res["ms_per_step"] * 1e-3) / 1e9
     Y0 = Ys[0].to(torch.float64).cpu().numpy()
     del mats
@@ -504,7 +508,7 @@ def summarize(res, w, storage, peaks, pipes, tc, extra=None):
     ph = res["phases"]
     roof = roofline(w, ph, storage, peaks, pipes, tc)
     out = {"value": res["gbs"], "unit": "GB/s", "ms_per_step": res["ms_per_step"],
-           "bytes_per_step": res["bytes_per_step"],
+           "bytes_per_step": res["bytes_per_step"], "tree_shape": res.get("tree_shape"),
            "phase_ms_per_step": {PHASES[k]: ph["ms"][k] / ph["steps"] for k in range(len(PHASES))},
            "roofline": roof}
     if extra:
@@ -940,6 +944,7 @@ def main():
         roof["step"]["frac"] = roof["step"]["achieved"] / roof["peak"]
     ph = head["phases"]
     roof["phase_ms_per_step"] = {PHASES[k]: ph["ms"][k] / ph["steps"] for k in range(len(PHASES))}
+    roof["tree_shape"] = head.get("tree_shape")
 
     out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

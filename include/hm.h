@@ -329,6 +329,17 @@ hm_status hm_matrix_set_path(hm_matrix* A, int32_t path);
  * same order, so the results are identical; 0 picks 2 when it fits. */
 hm_status hm_matrix_set_tree(hm_matrix* A, int32_t mode);
 
+/* Chooses the launch shape of the one-launch tree kernel (levels shared by a
+ * thread-block cluster, right-hand-side columns per cluster, operator-ring
+ * slots) for products with r columns by timing every shape that fits on this
+ * device (three launches each on the matrix's scratch), instead of the
+ * built-in cost estimate; later products with r columns use it.  No result
+ * changes: every shape sums in the same order.  Allocates the scratch for r
+ * columns if needed; synchronous.  *best_ms (may be NULL) receives the chosen
+ * shape's time per launch.  HM_EUNSUPPORTED when the tree runs as per-level
+ * kernels for this matrix. */
+hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, double* best_ms);
+
 /* Per-kernel timing of later products on this matrix: with enable = 1 every
  * kernel launch of a product is bracketed by CUDA events recorded on the
  * product's stream; enable = 0 stops recording.  Not for use under CUDA-graph

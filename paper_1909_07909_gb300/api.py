@@ -193,6 +193,16 @@ class Matrix:
         """Tree-phase kernels: 0 automatic, 1 per-level launches, 2 one cluster launch (when it fits)."""
         check(lib.hm_matrix_set_tree(self._h, int(mode)), "hm_matrix_set_tree")
 
+    def tune_tree(self, r):
+        """Time every tree-kernel launch shape for r columns and keep the fastest;
+        returns its time per launch in ms (None when the tree runs per level)."""
+        ms = C.c_double()
+        st = lib.hm_matrix_tune_tree(self._h, int(r), C.byref(ms))
+        if st == L.HM_EUNSUPPORTED:
+            return None
+        check(st, "hm_matrix_tune_tree")
+        return ms.value
+
     def profile(self, enable=True):
         """Bracket every kernel launch of later products with CUDA events."""
         check(lib.hm_matrix_profile(self._h, 1 if enable else 0), "hm_matrix_profile")

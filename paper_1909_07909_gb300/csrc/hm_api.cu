@@ -882,6 +882,18 @@ extern "C" hm_status hm_matrix_phase_times(hm_matrix* A, double ms[5], int64_t l
   return static_cast<EventProf*>(A->prof)->read(ms, launches);
 }
 
+extern "C" hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, double* best_ms) {
+  if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
+  if (r < 1) return fail(HM_EINVAL, "r < 1");
+  int dev_prev = -1;
+  cudaGetDevice(&dev_prev);
+  if (dev_prev != A->device) cudaSetDevice(A->device);
+  const hm_status s = tune_tree_cluster(A, r, best_ms);
+  if (dev_prev != A->device) cudaSetDevice(dev_prev);
+  if (s == HM_EUNSUPPORTED) return fail(HM_EUNSUPPORTED, "no cluster tree shape fits this matrix");
+  return s;
+}
+
 extern "C" hm_status hm_matrix_reserve(hm_matrix* A, int64_t r_max) {
   if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
   if (r_max < 1) return fail(HM_EINVAL, "r_max < 1");

@@ -941,6 +941,78 @@ bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r) {
   return A->tree_ok;
 }
 
+// Times every feasible launch shape of the cluster tree kernel for r
+// columns (levels shared by the cluster s, columns per cluster, ring slots)
+// on the matrix's scratch, three launches each after a warm-up, and keeps the
+// fastest for later products with r columns.  Every shape sums in the same
+// order, so the choice never changes a result.
+template <typename C>
+static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
+                             double* best_ms) {
+  const bool hss = (mv.kind == HM_HSS);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    set_error("tree tuning: event creation failed");
+    return HM_ECUDA;
+  }
+  TreeShape best{0, 0, 0};
+  double bms = 1e300;
+  const int smax = mv.p < TREE_MAX_S ? mv.p : TREE_MAX_S;
+  for (int s = (smax >= 2 ? 2 : smax); s <= smax; ++s) {
+    for (int rc = 1; rc <= 8; rc *= 2) {
+      for (int ns = hss ? 2 : 0; ns <= (hss ? TREE_MAX_NS : 0); ++ns) {
+        const TreeShape sh{s, rc, ns};
+        TreeLayout T;
+        if (!tree_fit<C>(mv, rc, s, ns, &T)) continue;
+        if (tree_active_rc<C>(mv, r, sh) <= 0) continue;
+        hm_status stt = tree_launch_shape<C>(mv, ws, r, st, false, sh);
+        if (stt != HM_OK) { cudaGetLastError(); continue; }
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < 3 && stt == HM_OK; ++k) stt = tree_launch_shape<C>(mv, ws, r, st, false, sh);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess || stt != HM_OK) { cudaGetLastError(); continue; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / 3 < bms) {
+          bms = ms / 3;
+          best = sh;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best.rc == 0) return HM_EUNSUPPORTED;
+  A->tree_s = best.s;
+  A->tree_rc = best.rc;
+  A->tree_ns = best.ns;
+  A->tree_ok = true;
+  A->tree_ok_r = r;
+  if (best_ms) *best_ms = bms;
+  return HM_OK;
+}
+
+hm_status tune_tree_cluster(hm_matrix* A, int64_t r, double* best_ms) {
+  const MatView mv = A->view();
+  const bool hss = (mv.kind == HM_HSS);
+  if (A->tree_mode == 1 || mv.p < (hss ? 1 : 2) || mv.p > 11) return HM_EUNSUPPORTED;
+  hm_status st = ensure_scratch(A, r);
+  if (st != HM_OK) return st;
+  Scratch ws = scratch_of(A, r);
+  ws.prof = nullptr;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("tree tuning: stream creation failed");
+    return HM_ECUDA;
+  }
+  st = (mv.storage == HM_F64) ? tune_shapes<double>(A, mv, ws, r, s, best_ms)
+                              : tune_shapes<float>(A, mv, ws, r, s, best_ms);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  return st;
+}
+
 hm_status launch_tree_cluster(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
                               bool pdl) {
   if (!tree_cluster_usable(A, mv, r)) return HM_EUNSUPPORTED;

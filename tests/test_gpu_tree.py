@@ -117,3 +117,26 @@ def test_set_tree_rejects_bad_mode():
     A = hm.Matrix.create(hm.Tree.from_leaf_ends(c), _gens("hss", c, 1, 4), "f32")
     with pytest.raises(hm.HMError):
         A.set_tree(3)
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+@pytest.mark.parametrize("name,kind,c,k,r", [CASES[3], CASES[4], CASES[8]])
+def test_tuned_tree_shape_changes_no_bit(storage, name, kind, c, k, r):
+    """hm_matrix_tune_tree picks a launch shape by timing; every shape sums in
+    the same order, so the product is bit-identical to the per-level kernels'."""
+    g = _gens(kind, c, 9, k)
+    n = int(c[-1])
+    xt = "f64" if storage == "f64" else "f32"
+    X = H.exact_input(np.random.default_rng(r).standard_normal((n, r)), xt)
+    A = hm.Matrix.create(hm.Tree.from_leaf_ends(c), g, storage)
+    Xd = H.to_dev(X, xt)
+    od = torch.float64 if storage == "f64" else torch.float32
+    A.set_tree(1)
+    y_level = H.to_host(A.matmat(Xd, out_dtype=od))
+    A.set_tree(0)
+    ms = A.tune_tree(r)
+    assert ms is not None and ms > 0
+    y_tuned = H.to_host(A.matmat(Xd, out_dtype=od))
+    info = A.info()
+    assert info["tree_cluster"] > 0
+    assert np.array_equal(y_level, y_tuned), name
