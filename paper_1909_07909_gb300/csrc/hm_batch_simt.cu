@@ -29,10 +29,10 @@ __device__ void expand_item(const BatchJob& J, const BatchIO& o, int bx, int by,
   using C = typename Stor<S>::C;
   const int leaf = bx / J.tiles, tile = bx % J.tiles;
 #define HM_E(RC_, TR_)                                                                                        \
-  expand_block<S, RC_, TR_, (RC_ <= 2 && S == HM_BF16) ? 1 : 2>(J.mv, J.ws, J.r, o.X, o.ldx, o.xt, o.Y, o.ldy, o.yt, J.RT, leaf, tile, by, \
+  expand_block<S, RC_, TR_>(J.mv, J.ws, J.r, o.X, o.ldx, o.xt, o.Y, o.ldy, o.yt, J.RT, leaf, tile, by, \
                             reinterpret_cast<C*>(sm));                                                       \
   break
-  constexpr int TRN = (S == HM_BF16) ? 8 : 4;   // as the single product's expansion
+  constexpr int TRN = 4;   // as the single product's expansion
   switch (J.rc_e) {
     case 1: HM_E(1, TRN);
     case 2: HM_E(2, TRN);
