@@ -323,7 +323,8 @@ def time_variant(hm, torch, tree, g, storage, X, steps, warmup, copies, clock_in
     tree_ms = None
     for A in mats:
         A.reserve(r)
-        tree_ms = A.tune_tree(r)   # the fastest launch shape of the tree kernel (no result changes)
+        # the fastest launch shape of the tree kernel for this product (no result changes)
+        tree_ms = A.tune_tree(r, X_DTYPE[storage], "f64" if storage == "f64" else "f32")
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     code = hm.HM_F64 if storage == "f64" else hm.HM_F32
@@ -391,6 +392,7 @@ def e2e_host(hm, torch, tree, g, storage, X, steps, copies):
     mats = [hm.Matrix.create(tree, g, storage) for _ in range(copies)]
     for A in mats:
         A.reserve(r)
+        A.tune_tree(r, X_DTYPE[storage], "f64" if storage == "f64" else "f32")
     f64 = storage == "f64"
     td = torch.float64 if f64 else torch.float32
     xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]

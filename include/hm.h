@@ -331,14 +331,17 @@ hm_status hm_matrix_set_tree(hm_matrix* A, int32_t mode);
 
 /* Chooses the launch shape of the one-launch tree kernel (levels shared by a
  * thread-block cluster, right-hand-side columns per cluster, operator-ring
- * slots) for products with r columns by timing every shape that fits on this
- * device (three launches each on the matrix's scratch), instead of the
- * built-in cost estimate; later products with r columns use it.  No result
- * changes: every shape sums in the same order.  Allocates the scratch for r
- * columns if needed; synchronous.  *best_ms (may be NULL) receives the chosen
- * shape's time per launch.  HM_EUNSUPPORTED when the tree runs as per-level
- * kernels for this matrix. */
-hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, double* best_ms);
+ * slots) for products with r columns of types xt, yt by timing the whole
+ * product (three each, on zero inputs) with every shape that fits on this
+ * device, instead of the built-in cost estimate; later products with r
+ * columns use the fastest.  The product is timed, not the tree alone,
+ * because the expansion starts while the tree drains and competes with it
+ * for SMs.  No result changes: every shape sums in the same order.
+ * Allocates the scratch for r columns if needed and temporary X, Y buffers;
+ * synchronous.  *best_ms (may be NULL) receives the chosen shape's time per
+ * product.  HM_EUNSUPPORTED when the tree runs as per-level kernels for this
+ * matrix (or F64 storage with other X, Y types). */
+hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, hm_dtype xt, hm_dtype yt, double* best_ms);
 
 /* Per-kernel timing of later products on this matrix: with enable = 1 every
  * kernel launch of a product is bracketed by CUDA events recorded on the

@@ -193,11 +193,17 @@ class Matrix:
         """Tree-phase kernels: 0 automatic, 1 per-level launches, 2 one cluster launch (when it fits)."""
         check(lib.hm_matrix_set_tree(self._h, int(mode)), "hm_matrix_set_tree")
 
-    def tune_tree(self, r):
-        """Time every tree-kernel launch shape for r columns and keep the fastest;
-        returns its time per launch in ms (None when the tree runs per level)."""
+    def tune_tree(self, r, xt=None, yt=None):
+        """Time the product for r columns with every tree-kernel launch shape and
+        keep the fastest; returns its time per product in ms (None when the tree
+        runs per level).  xt, yt: X and Y types (default F64 for F64 storage,
+        else F32)."""
+        info = self.info()
+        f64 = info["storage"] == L.HM_F64
+        xt = _dtype_code(xt) if xt is not None else (L.HM_F64 if f64 else L.HM_F32)
+        yt = _dtype_code(yt) if yt is not None else (L.HM_F64 if f64 else L.HM_F32)
         ms = C.c_double()
-        st = lib.hm_matrix_tune_tree(self._h, int(r), C.byref(ms))
+        st = lib.hm_matrix_tune_tree(self._h, int(r), int(xt), int(yt), C.byref(ms))
         if st == L.HM_EUNSUPPORTED:
             return None
         check(st, "hm_matrix_tune_tree")

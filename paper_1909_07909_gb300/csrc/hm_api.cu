@@ -882,13 +882,17 @@ extern "C" hm_status hm_matrix_phase_times(hm_matrix* A, double ms[5], int64_t l
   return static_cast<EventProf*>(A->prof)->read(ms, launches);
 }
 
-extern "C" hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, double* best_ms) {
+extern "C" hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, hm_dtype xt, hm_dtype yt, double* best_ms) {
   if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
   if (r < 1) return fail(HM_EINVAL, "r < 1");
+  if (xt != HM_F64 && xt != HM_F32 && xt != HM_BF16) return fail(HM_EINVAL, "X type must be F64, F32 or BF16");
+  if (yt != HM_F64 && yt != HM_F32) return fail(HM_EINVAL, "Y type must be F64 or F32");
+  if (A->storage == HM_F64 && (xt != HM_F64 || yt != HM_F64))
+    return fail(HM_EUNSUPPORTED, "F64 storage needs F64 X and Y");
   int dev_prev = -1;
   cudaGetDevice(&dev_prev);
   if (dev_prev != A->device) cudaSetDevice(A->device);
-  const hm_status s = tune_tree_cluster(A, r, best_ms);
+  const hm_status s = tune_tree_cluster(A, r, xt, yt, best_ms);
   if (dev_prev != A->device) cudaSetDevice(dev_prev);
   if (s == HM_EUNSUPPORTED) return fail(HM_EUNSUPPORTED, "no cluster tree shape fits this matrix");
   return s;

@@ -135,7 +135,7 @@ bool tc_plan(const hm_matrix* A, int64_t r, bool proj, int* nt, int* nK, int* nX
 hm_status launch_tree_cluster(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
                               bool pdl);
 bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r);
-hm_status tune_tree_cluster(hm_matrix* A, int64_t r, double* best_ms);
+hm_status tune_tree_cluster(hm_matrix* A, int64_t r, int xt, int yt, double* best_ms);
 hm_status launch_project_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                             int64_t ldx, int xt, cudaStream_t st, bool pdl);
 size_t tc_tile_smem(bool split, int NT, int nK, int nst);

@@ -32,7 +32,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cmath>
 #include <cstdint>
 
 #include "hm_internal.h"
@@ -844,38 +843,17 @@ hm_status launch_phase_rc(int phase, const MatView& mv, const Scratch& ws, int64
                  nchunks);
     prof_mark(ws.prof, 0, false, st);
   } else {
-    // rows per block: the largest tile (64, 128 or 256 rows) whose grid fills
-    // the resident block slots to at least 85 % in its last wave, so a block's
-    // fixed work (staging X and Z, barriers) is spread over many streamed rows
-    // without leaving SMs idle at the end; else the tile with the fullest last
-    // wave.  The row sums do not depend on it.
+    // rows per block: a whole leaf (up to 256 rows) when that still gives
+    // several blocks per SM, so a block's fixed work (staging X and Z,
+    // barriers) is spread over more streamed rows (smaller tiles that fill
+    // the last wave better measured slower); the row sums do not depend on it
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int RT = 64;
-    double best_eff = -1.0;
-    bool full = false;
-    for (int cand = 64; cand <= 256; cand *= 2) {
-      if (cand > 64 && cand >= 2 * mv.m_pad) break;
-      const size_t sm_c = sizeof(C) * static_cast<size_t>(RC * mv.We + RC * (cand + 1));
-      if (sm_c > 220 * 1024) break;
-      int per = 1;
-      cudaFuncSetAttribute(k_expand<S, RC, TR, UQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_c));
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_expand<S, RC, TR, UQ>, 256, sm_c) != cudaSuccess) {
-        cudaGetLastError();
-        per = 1;
-      }
-      const double blocks = static_cast<double>(mv.L) * ((mv.m_pad + cand - 1) / cand) * nchunks;
-      const double waves = blocks / (static_cast<double>(std::max(per, 1)) * sms);
-      const double eff = waves / std::ceil(waves);
-      if (eff >= 0.85) {
-        RT = cand;
-        full = true;
-      } else if (!full && eff > best_eff) {
-        RT = cand;
-        best_eff = eff;
-      }
-    }
+    while (RT < 256 && RT < mv.m_pad &&
+           static_cast<int64_t>(mv.L) * ((mv.m_pad + 2 * RT - 1) / (2 * RT)) * nchunks >= 4 * sms)
+      RT *= 2;
     const int tiles = (mv.m_pad + RT - 1) / RT;
     const size_t smem = sizeof(C) * static_cast<size_t>(RC * mv.We + RC * (RT + 1));
     if (smem > 220 * 1024) return HM_EUNSUPPORTED;

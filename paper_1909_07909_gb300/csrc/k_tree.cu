@@ -941,14 +941,17 @@ bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r) {
   return A->tree_ok;
 }
 
-// Times every feasible launch shape of the cluster tree kernel for r
-// columns (levels shared by the cluster s, columns per cluster, ring slots)
-// on the matrix's scratch, three launches each after a warm-up, and keeps the
-// fastest for later products with r columns.  Every shape sums in the same
-// order, so the choice never changes a result.
+// Times the whole product (projection, tree, expansion; the tree in one
+// cluster launch) for r columns with every launch shape of the tree kernel
+// that fits (levels shared by the cluster s, columns per cluster, ring
+// slots), on zero inputs of the given types, three products each after a
+// warm-up, and keeps the fastest for later products with r columns.  The
+// product, not the tree alone, is timed because the expansion starts while
+// the tree drains and competes with it for SMs.  Every shape sums in the
+// same order, so the choice never changes a result.
 template <typename C>
-static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
-                             double* best_ms) {
+static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X, int xt,
+                             void* Y, int yt, cudaStream_t st, double* best_ms) {
   const bool hss = (mv.kind == HM_HSS);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -956,9 +959,12 @@ static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws,
     set_error("tree tuning: event creation failed");
     return HM_ECUDA;
   }
+  const int mode = A->tree_mode;
+  A->tree_mode = 2;
   TreeShape best{0, 0, 0};
   double bms = 1e300;
   const int smax = mv.p < TREE_MAX_S ? mv.p : TREE_MAX_S;
+  const int64_t n = mv.n;
   for (int s = (smax >= 2 ? 2 : smax); s <= smax; ++s) {
     for (int rc = 1; rc <= 8; rc *= 2) {
       for (int ns = hss ? 2 : 0; ns <= (hss ? TREE_MAX_NS : 0); ++ns) {
@@ -966,10 +972,15 @@ static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws,
         TreeLayout T;
         if (!tree_fit<C>(mv, rc, s, ns, &T)) continue;
         if (tree_active_rc<C>(mv, r, sh) <= 0) continue;
-        hm_status stt = tree_launch_shape<C>(mv, ws, r, st, false, sh);
-        if (stt != HM_OK) { cudaGetLastError(); continue; }
+        A->tree_s = sh.s;
+        A->tree_rc = sh.rc;
+        A->tree_ns = sh.ns;
+        A->tree_ok = true;
+        A->tree_ok_r = r;
+        hm_status stt = launch_product(A, mv, ws, r, X, n, xt, Y, n, yt, st);
+        if (stt != HM_OK || !A->tree_last_cluster) { cudaGetLastError(); continue; }
         cudaEventRecord(e0, st);
-        for (int k = 0; k < 3 && stt == HM_OK; ++k) stt = tree_launch_shape<C>(mv, ws, r, st, false, sh);
+        for (int k = 0; k < 3 && stt == HM_OK; ++k) stt = launch_product(A, mv, ws, r, X, n, xt, Y, n, yt, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess || stt != HM_OK) { cudaGetLastError(); continue; }
         float ms = 0.f;
@@ -983,7 +994,11 @@ static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws,
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best.rc == 0) return HM_EUNSUPPORTED;
+  A->tree_mode = mode;
+  if (best.rc == 0) {
+    A->tree_ok_r = -1;   // fall back to the built-in choice
+    return HM_EUNSUPPORTED;
+  }
   A->tree_s = best.s;
   A->tree_rc = best.rc;
   A->tree_ns = best.ns;
@@ -993,7 +1008,7 @@ static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws,
   return HM_OK;
 }
 
-hm_status tune_tree_cluster(hm_matrix* A, int64_t r, double* best_ms) {
+hm_status tune_tree_cluster(hm_matrix* A, int64_t r, int xt, int yt, double* best_ms) {
   const MatView mv = A->view();
   const bool hss = (mv.kind == HM_HSS);
   if (A->tree_mode == 1 || mv.p < (hss ? 1 : 2) || mv.p > 11) return HM_EUNSUPPORTED;
@@ -1001,15 +1016,28 @@ hm_status tune_tree_cluster(hm_matrix* A, int64_t r, double* best_ms) {
   if (st != HM_OK) return st;
   Scratch ws = scratch_of(A, r);
   ws.prof = nullptr;
+  const size_t xs = (xt == HM_F64) ? 8 : (xt == HM_F32) ? 4 : 2;
+  const size_t ys = (yt == HM_F64) ? 8 : 4;
+  const size_t nr = static_cast<size_t>(std::max<int64_t>(mv.n, 1)) * r;
+  void* X = nullptr;
+  void* Y = nullptr;
   cudaStream_t s = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-    set_error("tree tuning: stream creation failed");
-    return HM_ECUDA;
+  cudaError_t e = dev_malloc(&X, nr * xs);
+  if (e == cudaSuccess) e = dev_malloc(&Y, nr * ys);
+  if (e == cudaSuccess) e = cudaMemset(X, 0, nr * xs);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    if (X) cudaFree(X);
+    if (Y) cudaFree(Y);
+    set_error("tree tuning: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA;
   }
-  st = (mv.storage == HM_F64) ? tune_shapes<double>(A, mv, ws, r, s, best_ms)
-                              : tune_shapes<float>(A, mv, ws, r, s, best_ms);
+  st = (mv.storage == HM_F64) ? tune_shapes<double>(A, mv, ws, r, X, xt, Y, yt, s, best_ms)
+                              : tune_shapes<float>(A, mv, ws, r, X, xt, Y, yt, s, best_ms);
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
+  cudaFree(X);
+  cudaFree(Y);
   return st;
 }
 
