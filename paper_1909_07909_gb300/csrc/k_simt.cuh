@@ -912,6 +912,12 @@ hm_status launch_tree_rc(int phase, const MatView& mv, const Scratch& ws, int64_
   return HM_OK;
 }
 
+// Leaf expansion for one or two columns with the plane streamed by bulk
+// copies (k_ring.cuh; instantiated by the per-storage units).
+template <int S, int RC, int TR>
+hm_status launch_expand_ring(const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx, int xt,
+                             void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl);
+
 // Phases: 0 projection, 1 tree upsweep / sums, 2 HSS downsweep, 3 leaf expansion.
 template <int S>
 hm_status simt_phase_t(int phase, const MatView& mv, const Scratch& ws, int64_t r, const void* X, int64_t ldx,
@@ -949,6 +955,13 @@ hm_status simt_phase_t(int phase, const MatView& mv, const Scratch& ws, int64_t 
   // one q step, for the short BF16 rows, measured slower: 0.50 vs 0.57 of HBM)
   constexpr int TRN = 4;
   constexpr int UQN = 2;
+  if constexpr (S != HM_F64) {
+    // one or two columns: the plane streamed through a ring of bulk copies
+    hm_status st_ring = HM_EUNSUPPORTED;
+    if (rc == 1) st_ring = launch_expand_ring<S, 1, TRN>(mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
+    else if (rc == 2) st_ring = launch_expand_ring<S, 2, TRN>(mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
+    if (st_ring != HM_EUNSUPPORTED) return st_ring;
+  }
   switch (rc) {
     case 1: HM_PHASE_U(1, TRN, UQN);
     case 2: HM_PHASE_U(2, TRN, UQN);

@@ -1,5 +1,5 @@
-// SIMT kernels instantiated for HM_F32 storage (see k_simt.cuh).
-#include "k_simt.cuh"
+// SIMT kernels instantiated for HM_F32 storage (see k_simt.cuh, k_ring.cuh).
+#include "k_ring.cuh"
 
 namespace hmi {
 

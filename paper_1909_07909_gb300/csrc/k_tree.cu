@@ -27,6 +27,7 @@
 // wait is bounded (the library's device wait limit, 2 s of %globaltimer by
 // default): on expiry the kernel records an error code in the library's
 // error word and stops waiting.
+#include <algorithm>
 #include <type_traits>
 
 #include "hm_api_internal.h"
@@ -963,6 +964,13 @@ static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws,
   A->tree_mode = 2;
   TreeShape best{0, 0, 0};
   double bms = 1e300;
+  // the built-in choice, kept unless a shape beats it by at least 2 %
+  TreeShape dflt{0, 0, 0};
+  const bool have_dflt = tree_pick<C>(mv, r, &dflt);
+  double dms = 1e300;
+  cudaEvent_t ev[6];
+  for (auto& x : ev) x = nullptr;
+  for (auto& x : ev) cudaEventCreate(&x);
   const int smax = mv.p < TREE_MAX_S ? mv.p : TREE_MAX_S;
   const int64_t n = mv.n;
   for (int s = (smax >= 2 ? 2 : smax); s <= smax; ++s) {
@@ -979,14 +987,20 @@ static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws,
         A->tree_ok_r = r;
         hm_status stt = launch_product(A, mv, ws, r, X, n, xt, Y, n, yt, st);
         if (stt != HM_OK || !A->tree_last_cluster) { cudaGetLastError(); continue; }
-        cudaEventRecord(e0, st);
-        for (int k = 0; k < 3 && stt == HM_OK; ++k) stt = launch_product(A, mv, ws, r, X, n, xt, Y, n, yt, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess || stt != HM_OK) { cudaGetLastError(); continue; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms / 3 < bms) {
-          bms = ms / 3;
+        // five products, each timed on its own; the median is the shape's time
+        cudaEventRecord(ev[0], st);
+        for (int k = 0; k < 5 && stt == HM_OK; ++k) {
+          stt = launch_product(A, mv, ws, r, X, n, xt, Y, n, yt, st);
+          cudaEventRecord(ev[k + 1], st);
+        }
+        if (cudaEventSynchronize(ev[5]) != cudaSuccess || stt != HM_OK) { cudaGetLastError(); continue; }
+        float t[5];
+        for (int k = 0; k < 5; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+        std::sort(t, t + 5);
+        const double med = t[2];
+        if (have_dflt && sh.s == dflt.s && sh.rc == dflt.rc && sh.ns == dflt.ns) dms = med;
+        if (med < bms) {
+          bms = med;
           best = sh;
         }
       }
@@ -994,7 +1008,13 @@ static hm_status tune_shapes(hm_matrix* A, const MatView& mv, const Scratch& ws,
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
   A->tree_mode = mode;
+  if (best.rc != 0 && dms < 1e300 && bms > 0.98 * dms) {
+    best = dflt;
+    bms = dms;
+  }
   if (best.rc == 0) {
     A->tree_ok_r = -1;   // fall back to the built-in choice
     return HM_EUNSUPPORTED;
