@@ -343,6 +343,18 @@ hm_status hm_matrix_set_tree(hm_matrix* A, int32_t mode);
  * matrix (or F64 storage with other X, Y types). */
 hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, hm_dtype xt, hm_dtype yt, double* best_ms);
 
+/* Pins the launch shape of the one-launch tree kernel for products of r
+ * columns (not in the paper): clusters of cluster_ctas CTAs (2, 4, 8 or 16,
+ * at most 2^depth), each cluster taking `columns` (1, 2, 4 or 8) of the
+ * right-hand-side columns, with ring_slots (2..12; 0 for HODLR) operator
+ * slots per CTA.  Every shape sums in the same order, so results do not
+ * depend on it; only the time does.  HM_EINVAL for values outside those
+ * sets; HM_EUNSUPPORTED when the shape does not fit this matrix in shared
+ * memory or no cluster of it can be resident, or when the tree runs as
+ * per-level kernels.  A later hm_matrix_tune_tree replaces it. */
+hm_status hm_matrix_set_tree_shape(hm_matrix* A, int64_t r, int32_t cluster_ctas, int32_t columns,
+                                   int32_t ring_slots);
+
 /* Per-kernel timing of later products on this matrix: with enable = 1 every
  * kernel launch of a product is bracketed by CUDA events recorded on the
  * product's stream; enable = 0 stops recording.  Not for use under CUDA-graph

@@ -88,6 +88,7 @@ _decl("hm_matrix_reserve", C.c_int, vp, C.c_int64)
 _decl("hm_matrix_set_path", C.c_int, vp, C.c_int32)
 _decl("hm_matrix_set_tree", C.c_int, vp, C.c_int32)
 _decl("hm_matrix_tune_tree", C.c_int, vp, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_double))
+_decl("hm_matrix_set_tree_shape", C.c_int, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32)
 _decl("hm_hodlr_matmat", C.c_int, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_int, vp)
 _decl("hm_hss_matmat", C.c_int, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_int, vp)
 _decl("hm_device_status", C.c_int, vp)

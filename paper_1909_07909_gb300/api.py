@@ -209,6 +209,13 @@ class Matrix:
         check(st, "hm_matrix_tune_tree")
         return ms.value
 
+    def set_tree_shape(self, r, cluster_ctas, columns, ring_slots):
+        """Pin the tree kernel's launch shape for products of r columns
+        (clusters of cluster_ctas CTAs, `columns` columns per cluster,
+        ring_slots operator slots; 0 for HODLR)."""
+        check(lib.hm_matrix_set_tree_shape(self._h, int(r), int(cluster_ctas), int(columns), int(ring_slots)),
+              "hm_matrix_set_tree_shape")
+
     def profile(self, enable=True):
         """Bracket every kernel launch of later products with CUDA events."""
         check(lib.hm_matrix_profile(self._h, 1 if enable else 0), "hm_matrix_profile")

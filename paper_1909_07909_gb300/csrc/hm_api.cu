@@ -898,6 +898,22 @@ extern "C" hm_status hm_matrix_tune_tree(hm_matrix* A, int64_t r, hm_dtype xt, h
   return s;
 }
 
+extern "C" hm_status hm_matrix_set_tree_shape(hm_matrix* A, int64_t r, int32_t cluster_ctas, int32_t columns,
+                                              int32_t ring_slots) {
+  if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
+  if (r < 1) return fail(HM_EINVAL, "r < 1");
+  int dev_prev = -1;
+  cudaGetDevice(&dev_prev);
+  if (dev_prev != A->device) cudaSetDevice(A->device);
+  const hm_status s = set_tree_shape(A, r, cluster_ctas, columns, ring_slots);
+  if (dev_prev != A->device) cudaSetDevice(dev_prev);
+  if (s == HM_EINVAL)
+    return fail(HM_EINVAL, "tree shape: cluster_ctas a power of two from 2 to 16 and at most 2^depth, columns 1, 2, "
+                           "4 or 8, ring_slots 2..12 for HSS and 0 for HODLR");
+  if (s == HM_EUNSUPPORTED) return fail(HM_EUNSUPPORTED, "this tree shape does not fit this matrix");
+  return s;
+}
+
 extern "C" hm_status hm_matrix_reserve(hm_matrix* A, int64_t r_max) {
   if (!A || A->magic != kMagicMatrix) return fail(HM_EINVAL, "not a matrix handle");
   if (r_max < 1) return fail(HM_EINVAL, "r_max < 1");

@@ -136,6 +136,7 @@ hm_status launch_tree_cluster(hm_matrix* A, const MatView& mv, const Scratch& ws
                               bool pdl);
 bool tree_cluster_usable(hm_matrix* A, const MatView& mv, int64_t r);
 hm_status tune_tree_cluster(hm_matrix* A, int64_t r, int xt, int yt, double* best_ms);
+hm_status set_tree_shape(hm_matrix* A, int64_t r, int cluster_ctas, int columns, int ring_slots);
 hm_status launch_project_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                             int64_t ldx, int xt, cudaStream_t st, bool pdl);
 size_t tc_tile_smem(bool split, int NT, int nK, int nst);

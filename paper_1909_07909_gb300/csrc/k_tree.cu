@@ -1061,6 +1061,33 @@ hm_status tune_tree_cluster(hm_matrix* A, int64_t r, int xt, int yt, double* bes
   return st;
 }
 
+template <typename C>
+static hm_status set_shape(hm_matrix* A, const MatView& mv, int64_t r, const TreeShape& sh) {
+  TreeLayout T;
+  if (!tree_fit<C>(mv, sh.rc, sh.s, sh.ns, &T)) return HM_EUNSUPPORTED;
+  if (tree_active_rc<C>(mv, r, sh) <= 0) return HM_EUNSUPPORTED;
+  A->tree_s = sh.s;
+  A->tree_rc = sh.rc;
+  A->tree_ns = sh.ns;
+  A->tree_ok = true;
+  A->tree_ok_r = r;
+  return HM_OK;
+}
+
+hm_status set_tree_shape(hm_matrix* A, int64_t r, int cluster_ctas, int columns, int ring_slots) {
+  const MatView mv = A->view();
+  const bool hss = (mv.kind == HM_HSS);
+  if (A->tree_mode == 1 || mv.p < (hss ? 1 : 2) || mv.p > 11) return HM_EUNSUPPORTED;
+  int s = 0;
+  while ((1 << s) < cluster_ctas && s < 30) ++s;
+  const int smax = mv.p < TREE_MAX_S ? mv.p : TREE_MAX_S;
+  if ((1 << s) != cluster_ctas || s < 1 || s > smax) return HM_EINVAL;
+  if (columns != 1 && columns != 2 && columns != 4 && columns != 8) return HM_EINVAL;
+  if (hss ? (ring_slots < 2 || ring_slots > TREE_MAX_NS) : ring_slots != 0) return HM_EINVAL;
+  const TreeShape sh{s, columns, ring_slots};
+  return (mv.storage == HM_F64) ? set_shape<double>(A, mv, r, sh) : set_shape<float>(A, mv, r, sh);
+}
+
 hm_status launch_tree_cluster(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, cudaStream_t st,
                               bool pdl) {
   if (!tree_cluster_usable(A, mv, r)) return HM_EUNSUPPORTED;

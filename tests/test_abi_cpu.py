@@ -80,6 +80,8 @@ def test_invalid_handles_rejected():
     assert L.lib.hm_hss_matmat(None, 1, None, 1, 0, None, 1, 0, None) == L.HM_EINVAL
     info = L.hm_matrix_info_t()
     assert L.lib.hm_matrix_info(None, C.byref(info)) == L.HM_EINVAL
+    assert L.lib.hm_matrix_set_tree_shape(None, 8, 4, 8, 3) == L.HM_EINVAL
+    assert L.lib.hm_matrix_set_tree_shape(C.cast(junk, vp), 8, 4, 8, 3) == L.HM_EINVAL
     L.lib.hm_destroy(None)
 
 

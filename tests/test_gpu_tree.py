@@ -140,3 +140,40 @@ def test_tuned_tree_shape_changes_no_bit(storage, name, kind, c, k, r):
     info = A.info()
     assert info["tree_cluster"] > 0
     assert np.array_equal(y_level, y_tuned), name
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_pinned_tree_shapes_change_no_bit(storage):
+    """hm_matrix_set_tree_shape: every shape that fits gives the per-level
+    kernels' bits; values outside the allowed sets are rejected."""
+    c = OT.default_leaf_ends(4096, 64)
+    g = _gens("hss", c, 9, 12)
+    n = int(c[-1])
+    r = 8
+    xt = "f64" if storage == "f64" else "f32"
+    X = H.exact_input(np.random.default_rng(5).standard_normal((n, r)), xt)
+    A = hm.Matrix.create(hm.Tree.from_leaf_ends(c), g, storage)
+    Xd = H.to_dev(X, xt)
+    od = torch.float64 if storage == "f64" else torch.float32
+    A.set_tree(1)
+    y_level = H.to_host(A.matmat(Xd, out_dtype=od))
+    A.set_tree(0)
+    tried = 0
+    for cl in (2, 4, 8, 16):
+        for cols in (1, 2, 4, 8):
+            for ns in (2, 3, 5, 8, 12):
+                try:
+                    A.set_tree_shape(r, cl, cols, ns)
+                except hm.HMError as e:
+                    assert e.status == hm._lib.HM_EUNSUPPORTED, (cl, cols, ns, e)
+                    continue
+                tried += 1
+                y = H.to_host(A.matmat(Xd, out_dtype=od))
+                info = A.info()
+                assert (info["tree_cluster"], info["tree_columns"], info["tree_ring"]) == (cl, cols, ns)
+                assert np.array_equal(y_level, y), (cl, cols, ns)
+    assert tried >= 8
+    for bad in ((3, 8, 3), (32, 8, 3), (4, 3, 3), (4, 8, 1), (4, 8, 13)):
+        with pytest.raises(hm.HMError) as ei:
+            A.set_tree_shape(r, *bad)
+        assert ei.value.status == hm._lib.HM_EINVAL, bad
