@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="skip the n=4096 and n=262144 workloads")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tree-shape", default="", help="pin the tree kernel shape 'cluster,columns,slots' (no tuning)")
     ap.add_argument("--no-solve", action="store_true", help="skip the HSS solve variant")
     ap.add_argument("--cpu-leaves", type=int, default=6, help="leaf row blocks in the CPU oracle sample")
     ap.add_argument("--workload", default="hss", choices=["hss", "exp", "hodlr4096", "batched", "serve"],
@@ -266,6 +267,24 @@ def roofline(w, phases, storage, peaks, pipes, tc):
 # Workloads
 # ---------------------------------------------------------------------------
 
+# --tree-shape: a pinned launch shape of the tree kernel (cluster CTAs,
+# columns, ring slots) instead of timing every shape; for profiler runs,
+# where the timings that pick a shape are distorted.
+TREE_SHAPE = None
+
+
+def pick_tree(A, r, storage):
+    """Pin the --tree-shape launch shape when given (and it fits), else time
+    every shape and keep the fastest; returns the tuned ms or None."""
+    if TREE_SHAPE is not None:
+        try:
+            A.set_tree_shape(r, *TREE_SHAPE)
+            return None
+        except Exception:
+            pass
+    return A.tune_tree(r, X_DTYPE[storage], "f64" if storage == "f64" else "f32")
+
+
 def make_inputs():
     import workloads as W
     rng = W.rng_named("hss_n65536_m256_k32_r64")
@@ -324,7 +343,7 @@ def time_variant(hm, torch, tree, g, storage, X, steps, warmup, copies, clock_in
     for A in mats:
         A.reserve(r)
         # the fastest launch shape of the tree kernel for this product (no result changes)
-        tree_ms = A.tune_tree(r, X_DTYPE[storage], "f64" if storage == "f64" else "f32")
+        tree_ms = pick_tree(A, r, storage)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     code = hm.HM_F64 if storage == "f64" else hm.HM_F32
@@ -392,7 +411,7 @@ def e2e_host(hm, torch, tree, g, storage, X, steps, copies):
     mats = [hm.Matrix.create(tree, g, storage) for _ in range(copies)]
     for A in mats:
         A.reserve(r)
-        A.tune_tree(r, X_DTYPE[storage], "f64" if storage == "f64" else "f32")
+        pick_tree(A, r, storage)
     f64 = storage == "f64"
     td = torch.float64 if f64 else torch.float32
     xd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[X_DTYPE[storage]]
@@ -894,7 +913,10 @@ def run_workload_only(args):
 
 
 def main():
+    global TREE_SHAPE
     args = parse()
+    if args.tree_shape:
+        TREE_SHAPE = tuple(int(v) for v in args.tree_shape.split(","))
     rank, local, world = dist_env()
     if args.impl == "reference":
         return run_reference(args)

@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "k_tc.cuh"
+#include "k_tc_persist.cuh"
 
 namespace hmi {
 
@@ -127,6 +128,20 @@ int tc_tile_ncols(bool split, int NT) { return tc_ncols_host(split, NT); }
 
 // Tensor map of a bf16 X block (rows inner, columns outer) with NT-column boxes,
 // when X qualifies for TMA (16-byte aligned, ldx a multiple of 8 elements).
+// FP32 view of the tree scratch for the Z block: rows of Ke floats, row
+// node * r + col, boxes of 4 rows by NT columns, no swizzle.
+static bool z_map(CUtensorMap* map, const void* base, int Ke, int64_t rows, int NT) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !base || Ke % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Ke), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Ke) * 4};
+  const cuuint32_t box[2] = {4, static_cast<cuuint32_t>(NT)};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static bool x_map(CUtensorMap* map, const void* X, int64_t n, int64_t r, int64_t ldx, int NT) {
   if ((reinterpret_cast<uintptr_t>(X) & 15) != 0 || (ldx & 7) != 0 || n < TC_KC) return false;
   return encode_2d(map, X, static_cast<uint64_t>(n), static_cast<uint64_t>(r), static_cast<uint64_t>(ldx) * 2, TC_KC,
@@ -199,8 +214,84 @@ static hm_status launch_leaf(hm_matrix* A, const MatView& mv, const Scratch& ws,
 #undef HM_TC
 }
 
+// The persistent expansion (k_tc_persist.cuh) for BF16 storage, used when
+// the one-item-per-CTA kernel would take more than one wave of CTAs (with
+// one wave every item's loads, multiplies and stores already overlap across
+// CTAs, and it finishes sooner after the tree kernels): as many stages as fit
+// beside the Z block and the control block, one CTA per SM.
+template <int NT>
+static hm_status launch_expand_tcp_nt(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                                      int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl,
+                                      int nK, int nX, int nst_old, int tiles) {
+  constexpr int TPT = (NT < 32) ? 32 : NT;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nchunks = (r + NT - 1) / NT;
+  {
+    // waves of the one-item-per-CTA kernel, with its own tile pairing
+    int mt_o = 1, nst_o = nst_old;
+    const int64_t ctas2 = static_cast<int64_t>(mv.L) * ((tiles + 1) / 2) * nchunks;
+    tc_pick_mt(false, NT, nK, tiles, ctas2, sms, &mt_o, &nst_o);
+    const int64_t ctas = static_cast<int64_t>(mv.L) * ((tiles + mt_o - 1) / mt_o) * nchunks;
+    const size_t sm_o = tc_smem(false, NT, nK, nst_o, mt_o);
+    const int per = sm_o <= 113 * 1024 ? 2 : 1;
+    if (ctas <= static_cast<int64_t>(per) * sms) return HM_EUNSUPPORTED;
+  }
+  const int mt = (tiles >= 2 && 2 * TPT <= 256) ? 2 : 1;
+  if (2 * mt * TPT > 512) return HM_EUNSUPPORTED;
+  int nst = TCP_MAX_STAGES;
+  while (nst > 2 && tcp_smem_bytes(NT, mt, nst, mv.Ke) > 227 * 1024) --nst;
+  const size_t smem = tcp_smem_bytes(NT, mt, nst, mv.Ke);
+  if (smem > 227 * 1024) return HM_EUNSUPPORTED;
+  const int tgroups = (tiles + mt - 1) / mt;
+  const int64_t nitems64 = static_cast<int64_t>(mv.L) * tgroups * nchunks;
+  if (nitems64 <= 0 || nitems64 > (int64_t(1) << 30)) return HM_EUNSUPPORTED;
+  const int grid = static_cast<int>(std::min<int64_t>(nitems64, sms));
+  CUtensorMap tmX;
+  std::memset(&tmX, 0, sizeof(tmX));
+  const int use_tmx = (xt == HM_BF16 && x_map(&tmX, X, mv.n, r, ldx, NT)) ? 1 : 0;
+  CUtensorMap tmZ;
+  std::memset(&tmZ, 0, sizeof(tmZ));
+  const void* zbase = (mv.kind == HM_HSS) ? ws.yf : ws.PS;
+  const int use_tmz = (mv.p >= 1 && z_map(&tmZ, zbase, mv.Ke, (2 * static_cast<int64_t>(mv.L) - 1) * r, NT)) ? 1 : 0;
+  if (cudaFuncSetAttribute(k_expand_tcp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return HM_EUNSUPPORTED;
+  }
+  Scratch wk = ws;
+  wk.prof = nullptr;
+  prof_mark(ws.prof, 3, true, st);
+  const cudaError_t e = launch_k(k_expand_tcp<NT>, dim3(grid), dim3(TCP_THREADS), smem, st, pdl, A->tmA, tmX,
+                                 use_tmx, tmZ, use_tmz, mv, wk, r, X, ldx, xt, Y, ldy, yt, tgroups, static_cast<int>(nchunks),
+                                 static_cast<int>(nitems64), nK, nX, nst, mt);
+  prof_mark(ws.prof, 3, false, st);
+  if (e != cudaSuccess) {
+    set_error("persistent tensor-core expansion launch failed: %s", cudaGetErrorString(e));
+    return HM_ECUDA;
+  }
+  return HM_OK;
+}
+
+static hm_status launch_expand_tcp(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                                   int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
+  if (A->storage != HM_BF16) return HM_EUNSUPPORTED;
+  int NT = 16, nK = 0, nX = 0, nst = 0, tiles = 0;
+  if (!tc_plan(A, r, false, &NT, &nK, &nX, &nst, &tiles)) return HM_EUNSUPPORTED;
+  switch (NT) {
+    case 16: return launch_expand_tcp_nt<16>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
+    case 32: return launch_expand_tcp_nt<32>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
+    case 64: return launch_expand_tcp_nt<64>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
+    case 128: return launch_expand_tcp_nt<128>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
+    default: return launch_expand_tcp_nt<256>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
+  }
+}
+
 hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                            int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
+  const hm_status s = launch_expand_tcp(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
+  if (s != HM_EUNSUPPORTED) return s;
   return launch_leaf<false>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
 }
 
