@@ -128,14 +128,37 @@ int tc_tile_ncols(bool split, int NT) { return tc_ncols_host(split, NT); }
 
 // Tensor map of a bf16 X block (rows inner, columns outer) with NT-column boxes,
 // when X qualifies for TMA (16-byte aligned, ldx a multiple of 8 elements).
+// Box height of the Z block's tensor boxes: the largest power of two up to
+// 256 (at least 4) such that every box lies in one node's rows (HSS: all Ke
+// rows; HODLR: each level's block starts and ends on a multiple of it, the
+// blocks tiling the Ke rows); 0 when there is none (cp.async fetch).
+static int z_box_rows(const MatView& mv) {
+  if (mv.p < 1 || mv.Ke % 4 != 0) return 0;
+  if (mv.kind != HM_HSS) {
+    int next = 0;
+    for (int l = 1; l <= mv.p; ++l) {
+      if (mv.koff[l] != next) return 0;
+      next += mv.kk[l];
+    }
+    if (next != mv.Ke) return 0;
+  }
+  for (int hb = 256; hb >= 4; hb /= 2) {
+    bool ok = mv.Ke % hb == 0;
+    if (mv.kind != HM_HSS)
+      for (int l = 1; ok && l <= mv.p; ++l) ok = (mv.koff[l] % hb == 0) && (mv.kk[l] % hb == 0);
+    if (ok) return hb;
+  }
+  return 0;
+}
+
 // FP32 view of the tree scratch for the Z block: rows of Ke floats, row
-// node * r + col, boxes of 4 rows by NT columns, no swizzle.
-static bool z_map(CUtensorMap* map, const void* base, int Ke, int64_t rows, int NT) {
+// node * r + col, boxes of hb rows by NT columns, no swizzle.
+static bool z_map(CUtensorMap* map, const void* base, int Ke, int64_t rows, int NT, int hb) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || !base || Ke % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Ke), static_cast<cuuint64_t>(rows)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Ke) * 4};
-  const cuuint32_t box[2] = {4, static_cast<cuuint32_t>(NT)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(hb), static_cast<cuuint32_t>(NT)};
   const cuuint32_t es[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -242,8 +265,11 @@ static hm_status launch_expand_tcp_nt(hm_matrix* A, const MatView& mv, const Scr
   if (2 * mt * TPT > 512) return HM_EUNSUPPORTED;
   int nst = TCP_MAX_STAGES;
   while (nst > 2 && tcp_smem_bytes(NT, mt, nst, mv.Ke) > 227 * 1024) --nst;
-  const size_t smem = tcp_smem_bytes(NT, mt, nst, mv.Ke);
-  if (smem > 227 * 1024) return HM_EUNSUPPORTED;
+  if (tcp_smem_bytes(NT, mt, nst, mv.Ke) > 227 * 1024) return HM_EUNSUPPORTED;
+  // all of an SM's shared memory, whatever the ring needs: the CTA has its SM
+  // to itself (no CTA of the tree kernels, which programmatic launch lets run
+  // at the same time, beside it)
+  const size_t smem = 227 * 1024;
   const int tgroups = (tiles + mt - 1) / mt;
   const int64_t nitems64 = static_cast<int64_t>(mv.L) * tgroups * nchunks;
   if (nitems64 <= 0 || nitems64 > (int64_t(1) << 30)) return HM_EUNSUPPORTED;
@@ -254,7 +280,8 @@ static hm_status launch_expand_tcp_nt(hm_matrix* A, const MatView& mv, const Scr
   CUtensorMap tmZ;
   std::memset(&tmZ, 0, sizeof(tmZ));
   const void* zbase = (mv.kind == HM_HSS) ? ws.yf : ws.PS;
-  const int use_tmz = (mv.p >= 1 && z_map(&tmZ, zbase, mv.Ke, (2 * static_cast<int64_t>(mv.L) - 1) * r, NT)) ? 1 : 0;
+  int zhb = z_box_rows(mv);
+  if (zhb > 0 && !z_map(&tmZ, zbase, mv.Ke, (2 * static_cast<int64_t>(mv.L) - 1) * r, NT, zhb)) zhb = 0;
   if (cudaFuncSetAttribute(k_expand_tcp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
       cudaSuccess) {
     cudaGetLastError();
@@ -264,7 +291,7 @@ static hm_status launch_expand_tcp_nt(hm_matrix* A, const MatView& mv, const Scr
   wk.prof = nullptr;
   prof_mark(ws.prof, 3, true, st);
   const cudaError_t e = launch_k(k_expand_tcp<NT>, dim3(grid), dim3(TCP_THREADS), smem, st, pdl, A->tmA, tmX,
-                                 use_tmx, tmZ, use_tmz, mv, wk, r, X, ldx, xt, Y, ldy, yt, tgroups, static_cast<int>(nchunks),
+                                 use_tmx, tmZ, zhb, mv, wk, r, X, ldx, xt, Y, ldy, yt, tgroups, static_cast<int>(nchunks),
                                  static_cast<int>(nitems64), nK, nX, nst, mt);
   prof_mark(ws.prof, 3, false, st);
   if (e != cudaSuccess) {

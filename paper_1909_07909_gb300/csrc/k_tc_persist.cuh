@@ -15,9 +15,9 @@
 //    rows of the tree kernels' output, FP32) is fetched whole into shared
 //    memory for the next item while this one is multiplied (after
 //    griddepcontrol.wait, before the first), and converted from there to
-//    bf16 straight into the stages.  The fetch is Ke/4 tiled TMA loads of 4
+//    bf16 straight into the stages.  The fetch is Ke/hb tiled TMA loads of hb
 //    rows by NT columns from the tree scratch viewed as a 2-D tensor (each
-//    4-row group lies in one level's block); per-thread loads, and even one
+//    box lies in one level's block); per-thread loads, and even one
 //    bulk copy per level and column, queued behind the SM's own stream of
 //    stage copies and took 30-80 k cycles per item.  Where the rows are not
 //    16-byte aligned the block comes by cp.async.  X rows of other types or
@@ -134,55 +134,50 @@ __device__ __forceinline__ void tcp_z_fetch(float* zr, const MatView& mv, const 
   }
 }
 
-// True when the Z block can come by 4 x NT tensor boxes: Ke a multiple of 4
-// and (HODLR) every level's block of rows starting and ending on a multiple
-// of 4, the blocks tiling the Ke rows.
-__device__ __forceinline__ bool tcp_z_tma_ok(const MatView& mv) {
-  if (mv.Ke % 4 != 0 || mv.p < 1) return false;
-  if (mv.kind == HM_HSS) return true;
-  int next = 0;
-  for (int l = 1; l <= mv.p; ++l) {
-    if (mv.koff[l] != next || mv.kk[l] % 4 != 0) return false;
-    next += mv.kk[l];
-  }
-  return next == mv.Ke;
-}
-
-// The Z block of one item by Ke/4 tiled TMA loads (one thread), completing on
-// `zbar`.  tmZ views the tree scratch (HSS: y-hat; HODLR: the T blocks) as a
-// 2-D FP32 tensor of Ke-float rows, row node * r + col.  Columns past r hold
-// other values (the next node's rows, or zeros past the end): their B columns
-// only feed output columns that are not stored.
+// The Z block of one item by Ke / hb tiled TMA loads of hb x NT boxes (one
+// thread), completing on `zbar`; Z(e, col0 + n) lands at zr[(e / hb) * NT *
+// hb + n * hb + e % hb].  tmZ views the tree scratch (HSS: y-hat; HODLR: the
+// T blocks) as a 2-D FP32 tensor of Ke-float rows, row node * r + col, and
+// every box lies in one node's rows (hb divides each level's block).
+// Columns past r hold other values (the next node's rows, or zeros past the
+// end): their B columns only feed output columns that are not stored.
 __device__ __forceinline__ void tcp_z_fetch_tma(float* zr, uint32_t zbar, const CUtensorMap* tmZ, const MatView& mv,
-                                                int64_t r, int leaf, int col0, int NT) {
-  const int nq = mv.Ke / 4;
-  mbar_expect_tx(zbar, static_cast<uint32_t>(nq) * NT * 16);
+                                                int64_t r, int leaf, int col0, int NT, int hb) {
+  const int nq = mv.Ke / hb;
+  mbar_expect_tx(zbar, static_cast<uint32_t>(mv.Ke) * NT * 4);
   for (int q = 0; q < nq; ++q) {
+    const int e0 = q * hb;
     int node;
     if (mv.kind == HM_HSS) {
       node = mv.L - 1 + leaf;
     } else {
       int l = 1;
-      while (l < mv.p && 4 * q >= mv.koff[l] + mv.kk[l]) ++l;
+      while (l < mv.p && e0 >= mv.koff[l] + mv.kk[l]) ++l;
       const int anc = (1 << l) - 1 + (leaf >> (mv.p - l));
       node = (anc & 1) ? anc + 1 : anc - 1;
     }
-    tma_load_2d(smem_u32(zr + q * NT * 4), tmZ, 4 * q, static_cast<int>(node * r + col0), zbar);
+    tma_load_2d(smem_u32(zr + static_cast<size_t>(q) * NT * hb), tmZ, e0, static_cast<int>(node * r + col0), zbar);
   }
 }
 
 // B rows [c*64, c*64 + 64) of a chunk holding only Z and zero rows (c*64 >=
-// m_pad), from the Z block in shared memory, in the K-major swizzled layout
-// of stage_b (the same bf16 rounding of the same FP32 values).  Consecutive
-// threads take consecutive columns (conflict-free reads of the block).
+// m_pad), from the Z block in shared memory (box height hb), in the K-major
+// swizzled layout of stage_b (the same bf16 rounding of the same FP32
+// values).  Consecutive threads take consecutive columns.
 template <int NT>
-__device__ __forceinline__ void tcp_z_convert(uint8_t* sb, const float* zr, int Ke, int kz0, int stid) {
+__device__ __forceinline__ void tcp_z_convert(uint8_t* sb, const float* zr, int Ke, int hb, int kz0, int stid) {
   for (int it = stid; it < NT * 8; it += 64) {
     const int n = it % NT;
     const int un = it / NT;
     const int e0 = kz0 + un * 8;                   // first Z row of this 8-row group (a multiple of 8)
     float v[8];
-    if (e0 + 8 <= Ke) {
+    if (e0 + 8 <= Ke && hb % 8 == 0) {
+      const float* p = zr + (e0 / hb) * NT * hb + n * hb + (e0 % hb);
+      const float4 lo = *reinterpret_cast<const float4*>(p);
+      const float4 hi4 = *reinterpret_cast<const float4*>(p + 4);
+      v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+      v[4] = hi4.x; v[5] = hi4.y; v[6] = hi4.z; v[7] = hi4.w;
+    } else if (e0 + 8 <= Ke && hb == 4) {
       const float4 lo = *reinterpret_cast<const float4*>(zr + (e0 >> 2) * NT * 4 + n * 4);
       const float4 hi4 = *reinterpret_cast<const float4*>(zr + ((e0 >> 2) + 1) * NT * 4 + n * 4);
       v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
@@ -191,7 +186,7 @@ __device__ __forceinline__ void tcp_z_convert(uint8_t* sb, const float* zr, int 
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int e = e0 + j;
-        v[j] = (e < Ke) ? zr[(e >> 2) * NT * 4 + n * 4 + (e & 3)] : 0.f;
+        v[j] = (e < Ke) ? zr[(e / hb) * NT * hb + n * hb + (e % hb)] : 0.f;
       }
     }
     uint4 hi;
@@ -227,7 +222,7 @@ __device__ __forceinline__ TcpItem tcp_item(const MatView& mv, int it, int tgrou
 template <int NT>
 __global__ void __launch_bounds__(TCP_THREADS, 1)
     k_expand_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int use_tmx,
-                 const __grid_constant__ CUtensorMap tmZ, int use_tmz, MatView mv, Scratch ws, int64_t r, const void* X, int64_t ldx, int xt, void* Y, int64_t ldy, int yt,
+                 const __grid_constant__ CUtensorMap tmZ, int zhb, MatView mv, Scratch ws, int64_t r, const void* X, int64_t ldx, int xt, void* Y, int64_t ldy, int yt,
                  int tgroups, int nchunks, int nitems, int nK, int nX, int nst, int mt) {
   constexpr int A_BYTES = TC_M * TC_KC * 2;
   constexpr int BCH = NT * 128;
@@ -360,7 +355,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     int g = 0;
     bool stop = false;
     int zitem = -1;                                             // item whose Z block was requested into zr
-    const bool zbulk = use_tmz && tcp_z_tma_ok(mv);
+    const bool zbulk = zhb > 0;                                 // Z block by tensor boxes
     bool zpend = false;                                         // bulk copies in flight on zbar
     int zphase = 0;
     // some chunk holds only Z (and zero) rows: the ones converted from the Z block
@@ -399,7 +394,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
             fence_proxy_async();
             if (zbulk) {
               named_bar_sync(2, 64);                            // every thread's fence before the copies
-              if (stid == 0) tcp_z_fetch_tma(zr, zbar, &tmZ, mv, r, w.leaf, w.col0, NT);
+              if (stid == 0) tcp_z_fetch_tma(zr, zbar, &tmZ, mv, r, w.leaf, w.col0, NT, zhb);
             } else {
               tcp_z_fetch<NT>(zr, mv, ws, r, w.leaf, w.col0, stid);
             }
@@ -426,7 +421,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
         }
         uint8_t* sb = base + static_cast<size_t>(s) * SB + mt * A_BYTES;
         if (zfast) {
-          tcp_z_convert<NT>(sb, zr, mv.Ke, c * TC_KC - mv.m_pad, stid);
+          tcp_z_convert<NT>(sb, zr, mv.Ke, zbulk ? zhb : 4, c * TC_KC - mv.m_pad, stid);
         } else {
           // stage_b addresses chunk c at c * BCH from its base
           stage_b<false, NT>(sb - static_cast<size_t>(c) * BCH, nullptr, c * TC_KC, (c + 1) * TC_KC, stid, 64, mv, ws,
@@ -446,7 +441,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
           fence_proxy_async();                                  // this item's reads of zr before the copies
           if (zbulk) {
             named_bar_sync(2, 64);                              // every thread's fence before the copies
-            if (stid == 0) tcp_z_fetch_tma(zr, zbar, &tmZ, mv, r, w2.leaf, w2.col0, NT);
+            if (stid == 0) tcp_z_fetch_tma(zr, zbar, &tmZ, mv, r, w2.leaf, w2.col0, NT, zhb);
             zpend = true;
           } else {
             tcp_z_fetch<NT>(zr, mv, ws, r, w2.leaf, w2.col0, stid);
