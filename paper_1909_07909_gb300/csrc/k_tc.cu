@@ -237,15 +237,15 @@ static hm_status launch_leaf(hm_matrix* A, const MatView& mv, const Scratch& ws,
 #undef HM_TC
 }
 
-// The persistent expansion (k_tc_persist.cuh) for BF16 storage, used when
+// The persistent leaf kernels (k_tc_persist.cuh) for BF16 storage, used when
 // the one-item-per-CTA kernel would take more than one wave of CTAs (with
 // one wave every item's loads, multiplies and stores already overlap across
-// CTAs, and it finishes sooner after the tree kernels): as many stages as fit
-// beside the Z block and the control block, one CTA per SM.
-template <int NT>
-static hm_status launch_expand_tcp_nt(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
-                                      int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl,
-                                      int nK, int nX, int nst_old, int tiles) {
+// CTAs, and the expansion finishes sooner after the tree kernels): as many
+// stages as fit beside the Z block and the control block, one CTA per SM.
+template <int NT, bool PROJ>
+static hm_status launch_tcp_nt(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                               int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl, int nK,
+                               int nX, int nst_old, int tiles) {
   constexpr int TPT = (NT < 32) ? 32 : NT;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -254,21 +254,24 @@ static hm_status launch_expand_tcp_nt(hm_matrix* A, const MatView& mv, const Scr
   {
     // waves of the one-item-per-CTA kernel, with its own tile pairing
     int mt_o = 1, nst_o = nst_old;
-    const int64_t ctas2 = static_cast<int64_t>(mv.L) * ((tiles + 1) / 2) * nchunks;
-    tc_pick_mt(false, NT, nK, tiles, ctas2, sms, &mt_o, &nst_o);
+    if (!PROJ) {
+      const int64_t ctas2 = static_cast<int64_t>(mv.L) * ((tiles + 1) / 2) * nchunks;
+      tc_pick_mt(false, NT, nK, tiles, ctas2, sms, &mt_o, &nst_o);
+    }
     const int64_t ctas = static_cast<int64_t>(mv.L) * ((tiles + mt_o - 1) / mt_o) * nchunks;
     const size_t sm_o = tc_smem(false, NT, nK, nst_o, mt_o);
     const int per = sm_o <= 113 * 1024 ? 2 : 1;
     if (ctas <= static_cast<int64_t>(per) * sms) return HM_EUNSUPPORTED;
   }
+  const int ke = PROJ ? 0 : mv.Ke;
   const int mt = (tiles >= 2 && 2 * TPT <= 256) ? 2 : 1;
   if (2 * mt * TPT > 512) return HM_EUNSUPPORTED;
   int nst = TCP_MAX_STAGES;
-  while (nst > 2 && tcp_smem_bytes(NT, mt, nst, mv.Ke) > 227 * 1024) --nst;
-  if (tcp_smem_bytes(NT, mt, nst, mv.Ke) > 227 * 1024) return HM_EUNSUPPORTED;
+  while (nst > 2 && tcp_smem_bytes(NT, mt, nst, ke) > 227 * 1024) --nst;
+  if (tcp_smem_bytes(NT, mt, nst, ke) > 227 * 1024) return HM_EUNSUPPORTED;
   // all of an SM's shared memory, whatever the ring needs: the CTA has its SM
-  // to itself (no CTA of the tree kernels, which programmatic launch lets run
-  // at the same time, beside it)
+  // to itself (no CTA of the neighbouring kernels, which programmatic launch
+  // lets run at the same time, beside it)
   const size_t smem = 227 * 1024;
   const int tgroups = (tiles + mt - 1) / mt;
   const int64_t nitems64 = static_cast<int64_t>(mv.L) * tgroups * nchunks;
@@ -279,51 +282,61 @@ static hm_status launch_expand_tcp_nt(hm_matrix* A, const MatView& mv, const Scr
   const int use_tmx = (xt == HM_BF16 && x_map(&tmX, X, mv.n, r, ldx, NT)) ? 1 : 0;
   CUtensorMap tmZ;
   std::memset(&tmZ, 0, sizeof(tmZ));
-  const void* zbase = (mv.kind == HM_HSS) ? ws.yf : ws.PS;
-  int zhb = z_box_rows(mv);
-  if (zhb > 0 && !z_map(&tmZ, zbase, mv.Ke, (2 * static_cast<int64_t>(mv.L) - 1) * r, NT, zhb)) zhb = 0;
-  if (cudaFuncSetAttribute(k_expand_tcp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-      cudaSuccess) {
+  int zhb = 0;
+  if (!PROJ) {
+    const void* zbase = (mv.kind == HM_HSS) ? ws.yf : ws.PS;
+    zhb = z_box_rows(mv);
+    if (zhb > 0 && !z_map(&tmZ, zbase, mv.Ke, (2 * static_cast<int64_t>(mv.L) - 1) * r, NT, zhb)) zhb = 0;
+  }
+  if (cudaFuncSetAttribute(k_expand_tcp<NT, PROJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess) {
     cudaGetLastError();
     return HM_EUNSUPPORTED;
   }
   Scratch wk = ws;
   wk.prof = nullptr;
-  prof_mark(ws.prof, 3, true, st);
-  const cudaError_t e = launch_k(k_expand_tcp<NT>, dim3(grid), dim3(TCP_THREADS), smem, st, pdl, A->tmA, tmX,
-                                 use_tmx, tmZ, zhb, mv, wk, r, X, ldx, xt, Y, ldy, yt, tgroups, static_cast<int>(nchunks),
-                                 static_cast<int>(nitems64), nK, nX, nst, mt);
-  prof_mark(ws.prof, 3, false, st);
+  const int phase = PROJ ? 0 : 3;
+  prof_mark(ws.prof, phase, true, st);
+  const cudaError_t e =
+      launch_k(k_expand_tcp<NT, PROJ>, dim3(grid), dim3(TCP_THREADS), smem, st, pdl, PROJ ? A->tmW : A->tmA, tmX,
+               use_tmx, tmZ, zhb, mv, wk, r, X, ldx, xt, Y, ldy, yt, tgroups, static_cast<int>(nchunks),
+               static_cast<int>(nitems64), nK, nX, nst, mt, PROJ ? A->w_box : TC_M);
+  prof_mark(ws.prof, phase, false, st);
   if (e != cudaSuccess) {
-    set_error("persistent tensor-core expansion launch failed: %s", cudaGetErrorString(e));
+    set_error("persistent tensor-core leaf launch failed: %s", cudaGetErrorString(e));
     return HM_ECUDA;
   }
   return HM_OK;
 }
 
-static hm_status launch_expand_tcp(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
-                                   int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
+template <bool PROJ>
+static hm_status launch_tcp(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
+                            int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
   if (A->storage != HM_BF16) return HM_EUNSUPPORTED;
   int NT = 16, nK = 0, nX = 0, nst = 0, tiles = 0;
-  if (!tc_plan(A, r, false, &NT, &nK, &nX, &nst, &tiles)) return HM_EUNSUPPORTED;
+  if (!tc_plan(A, r, PROJ, &NT, &nK, &nX, &nst, &tiles)) return HM_EUNSUPPORTED;
+#define HM_TCP(N) return launch_tcp_nt<N, PROJ>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles)
   switch (NT) {
-    case 16: return launch_expand_tcp_nt<16>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
-    case 32: return launch_expand_tcp_nt<32>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
-    case 64: return launch_expand_tcp_nt<64>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
-    case 128: return launch_expand_tcp_nt<128>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
-    default: return launch_expand_tcp_nt<256>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl, nK, nX, nst, tiles);
+    case 16: HM_TCP(16);
+    case 32: HM_TCP(32);
+    case 64: HM_TCP(64);
+    case 128: HM_TCP(128);
+    default: HM_TCP(256);
   }
+#undef HM_TCP
 }
 
 hm_status launch_expand_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                            int64_t ldx, int xt, void* Y, int64_t ldy, int yt, cudaStream_t st, bool pdl) {
-  const hm_status s = launch_expand_tcp(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
+  const hm_status s = launch_tcp<false>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
   if (s != HM_EUNSUPPORTED) return s;
   return launch_leaf<false>(A, mv, ws, r, X, ldx, xt, Y, ldy, yt, st, pdl);
 }
 
 hm_status launch_project_tc(hm_matrix* A, const MatView& mv, const Scratch& ws, int64_t r, const void* X,
                             int64_t ldx, int xt, cudaStream_t st, bool pdl) {
+  const hm_status s = launch_tcp<true>(A, mv, ws, r, X, ldx, xt, nullptr, 0, 0, st, pdl);
+  if (s != HM_EUNSUPPORTED) return s;
   return launch_leaf<true>(A, mv, ws, r, X, ldx, xt, nullptr, 0, 0, st, pdl);
 }
 

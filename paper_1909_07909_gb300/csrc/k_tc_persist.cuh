@@ -206,7 +206,9 @@ struct TcpItem {
 
 // Item it: column chunk fastest, then tile group, then leaf (consecutive CTAs
 // take the column chunks of the same rows, which then hit in L2).
-__device__ __forceinline__ TcpItem tcp_item(const MatView& mv, int it, int tgroups, int nchunks, int NT, int mt) {
+// The projection (proj) has Kp output rows per leaf, the expansion m.
+__device__ __forceinline__ TcpItem tcp_item(const MatView& mv, int it, int tgroups, int nchunks, int NT, int mt,
+                                            bool proj = false) {
   TcpItem w;
   const int chunk = it % nchunks;
   const int tg = (it / nchunks) % tgroups;
@@ -215,15 +217,19 @@ __device__ __forceinline__ TcpItem tcp_item(const MatView& mv, int it, int tgrou
   w.m = static_cast<int>(mv.off[w.leaf + 1] - w.a0);
   w.t0 = tg * TC_M * mt;
   w.col0 = chunk * NT;
-  w.valid = w.t0 < w.m;
+  w.valid = w.t0 < (proj ? mv.Kp : w.m);
   return w;
 }
 
-template <int NT>
+// PROJ: the leaf projection P_i = Wprj_i X_i instead (Sec. 4.1; A = the
+// projection plane, box_rows of each 128-row tile loaded, K = m_pad, no Z
+// rows), written to the tree scratch as k_tc.cuh writes it.
+template <int NT, bool PROJ>
 __global__ void __launch_bounds__(TCP_THREADS, 1)
     k_expand_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int use_tmx,
-                 const __grid_constant__ CUtensorMap tmZ, int zhb, MatView mv, Scratch ws, int64_t r, const void* X, int64_t ldx, int xt, void* Y, int64_t ldy, int yt,
-                 int tgroups, int nchunks, int nitems, int nK, int nX, int nst, int mt) {
+                 const __grid_constant__ CUtensorMap tmZ, int zhb, MatView mv, Scratch ws, int64_t r, const void* X,
+                 int64_t ldx, int xt, void* Y, int64_t ldy, int yt, int tgroups, int nchunks, int nitems, int nK,
+                 int nX, int nst, int mt, int box_rows) {
   constexpr int A_BYTES = TC_M * TC_KC * 2;
   constexpr int BCH = NT * 128;
   constexpr uint32_t IDESC = idesc_bf16(TC_M, NT);
@@ -233,7 +239,8 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
   const uint32_t raw_s = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
   const int SB = mt * A_BYTES + BCH;
-  const int ke4 = tcp_ke4(mv.Ke);
+  const int ke = PROJ ? 0 : mv.Ke;                   // Z rows of the operand
+  const int ke4 = tcp_ke4(ke);
   float* zr = reinterpret_cast<float*>(base + static_cast<size_t>(nst) * SB);
   uint8_t* ctl = base + static_cast<size_t>(nst) * SB + static_cast<size_t>(NT) * ke4 * 4;
   const uint32_t full0 = smem_u32(ctl);                          // nst barriers, 2 arrivals + bytes
@@ -280,11 +287,11 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
       int g = 0;
       for (int it = blockIdx.x; it < nitems && !*s_dead; it += G) {
-        const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt);
+        const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt, PROJ);
         if (!w.valid) continue;
         const bool x_tma = use_tmx && xt == HM_BF16 && w.m == mv.m_pad && (w.a0 & 7) == 0;
         const int nXt = x_tma ? nX : 0;
-        const int a_row = static_cast<int>(w.a0 + w.t0);
+        const int a_row = PROJ ? w.leaf * mv.Kp + w.t0 : static_cast<int>(w.a0 + w.t0);
         for (int c = 0; c < nK; ++c, ++g) {
           const int s = g % nst;
           const int u = g / nst;
@@ -293,7 +300,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
             break;
           }
           const uint32_t st = smem_u32(base + static_cast<size_t>(s) * SB);
-          const uint32_t bytes = static_cast<uint32_t>(mt * A_BYTES + (c < nXt ? BCH : 0));
+          const uint32_t bytes = static_cast<uint32_t>(mt * (PROJ ? box_rows * TC_KC * 2 : A_BYTES) + (c < nXt ? BCH : 0));
           mbar_expect_tx(full0 + 8 * s, bytes);                 // arrival 1: the A tiles (and X)
           for (int t = 0; t < mt; ++t) tma_load_2d(st + t * A_BYTES, &tmA, c * TC_KC, a_row + t * TC_M, full0 + 8 * s);
           if (c < nXt) {
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     if (lane == 0) {
       int g = 0, kk = 0;
       for (int it = blockIdx.x; it < nitems && !*s_dead; it += G) {
-        const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt);
+        const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt, PROJ);
         if (!w.valid) continue;
         const int b = kk & 1;
         const int ub = kk >> 1;
@@ -359,9 +366,9 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     bool zpend = false;                                         // bulk copies in flight on zbar
     int zphase = 0;
     // some chunk holds only Z (and zero) rows: the ones converted from the Z block
-    const bool zany = ((mv.m_pad + TC_KC - 1) / TC_KC) * TC_KC < mv.m_pad + mv.Ke;
+    const bool zany = ((mv.m_pad + TC_KC - 1) / TC_KC) * TC_KC < mv.m_pad + ke;
     for (int it = blockIdx.x; it < nitems && !stop; it += G) {
-      const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt);
+      const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt, PROJ);
       if (!w.valid) continue;
       const bool x_tma = use_tmx && xt == HM_BF16 && w.m == mv.m_pad && (w.a0 & 7) == 0;
       const int nXt = x_tma ? nX : 0;
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
           stop = true;
           break;
         }
-        const bool zrows = (c + 1) * TC_KC > mv.m_pad && c * TC_KC < mv.m_pad + mv.Ke;
+        const bool zrows = (c + 1) * TC_KC > mv.m_pad && c * TC_KC < mv.m_pad + ke;
         if (zrows && !waited) {
           pdl_wait();                                           // Z is written by the tree kernels
           waited = true;
@@ -425,7 +432,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
         } else {
           // stage_b addresses chunk c at c * BCH from its base
           stage_b<false, NT>(sb - static_cast<size_t>(c) * BCH, nullptr, c * TC_KC, (c + 1) * TC_KC, stid, 64, mv, ws,
-                             r, w.leaf, w.a0, w.m, mv.Ke, w.col0, X, ldx, xt);
+                             r, w.leaf, w.a0, w.m, ke, w.col0, X, ldx, xt);
         }
         fence_proxy_async();
         named_bar_sync(2, 64);
@@ -436,7 +443,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
       // free: this item's chunks are converted, behind the barrier above)
       if (waited && zany) {
         for (int it2 = it + G; it2 < nitems; it2 += G) {
-          const TcpItem w2 = tcp_item(mv, it2, tgroups, nchunks, NT, mt);
+          const TcpItem w2 = tcp_item(mv, it2, tgroups, nchunks, NT, mt, PROJ);
           if (!w2.valid) continue;
           fence_proxy_async();                                  // this item's reads of zr before the copies
           if (zbulk) {
@@ -462,7 +469,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     const int row = ew * 32 + lane;
     int kk = 0;
     for (int it = blockIdx.x; it < nitems; it += G) {
-      const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt);
+      const TcpItem w = tcp_item(mv, it, tgroups, nchunks, NT, mt, PROJ);
       if (!w.valid) continue;
       const int b = kk & 1;
       const int ub = kk >> 1;
@@ -475,9 +482,12 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
       }
       tc_fence_after();
       const uint32_t lane_addr = tmem + static_cast<uint32_t>(b) * ACC + (static_cast<uint32_t>(ew * 32) << 16);
+      const int node = mv.L - 1 + w.leaf;
+      const int ldo = (mv.kind == HM_HODLR) ? mv.Ke : mv.Kp;
+      float* pout = static_cast<float*>(mv.kind == HM_HODLR ? ws.PS : ws.xh);
       for (int t = 0; t < mt; ++t) {
         const int tu = w.t0 + t * TC_M;
-        const int nrows = w.m - tu;
+        const int nrows = (PROJ ? mv.Kp : w.m) - tu;
         for (int cb = wg * 16; cb < NT; cb += 16 * TCP_EPI_WG) {
           float v[16];
           tmem_ld16(lane_addr + t * TPT + cb, v);
@@ -486,9 +496,13 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
             for (int j = 0; j < 16; ++j) {
               const int64_t col = w.col0 + cb + j;
               if (col < r) {
-                const int64_t idx = (w.a0 + tu + row) + col * ldy;
-                if (yt == HM_F64) static_cast<double*>(Y)[idx] = v[j];
-                else static_cast<float*>(Y)[idx] = v[j];
+                if constexpr (PROJ) {
+                  pout[(static_cast<int64_t>(node) * r + col) * ldo + tu + row] = v[j];
+                } else {
+                  const int64_t idx = (w.a0 + tu + row) + col * ldy;
+                  if (yt == HM_F64) static_cast<double*>(Y)[idx] = v[j];
+                  else static_cast<float*>(Y)[idx] = v[j];
+                }
               }
             }
           }

@@ -1,9 +1,9 @@
-"""The persistent tensor-core expansion (BF16 storage, many leaves).
+"""The persistent tensor-core leaf kernels (BF16 storage, many leaves).
 
-When the one-item-per-CTA expansion would need more than one wave of CTAs,
-single products run the persistent kernel (k_tc_persist.cuh): same MMA
-sequence, B chunks from TMA, from the Z block fetched into shared memory, or
-converted from global memory.  The batched path still runs the one-item-per-CTA
+When the one-item-per-CTA projection or expansion would need more than one
+wave of CTAs, single products run the persistent kernels (k_tc_persist.cuh):
+same MMA sequence, B chunks from TMA, from the Z block fetched into shared
+memory, or converted from global memory.  The batched path still runs the one-item-per-CTA
 tile code, so a batch of the same matrix must give the same bits; the results
 are also held to the oracle's bound (Sec. 4.1, Def. 2.2 / 2.3) on sampled
 rows.  Cases cover bf16 X by TMA, f32 X and bf16 X at an odd leading
