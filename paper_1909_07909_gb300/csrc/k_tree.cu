@@ -630,8 +630,11 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
       run_level_cw<C, RC>(R, mv, ws.err, la, pick_cw<RC>(nn * ((lev > 0 ? nbp : 0) + 2 * nbe), nwarps));
       k += nn;
     } else {
-      // HODLR: T_q = T_a + T_b over the rows of levels 1..lev, written out for every node
+      // HODLR: T_q = T_a + T_b over the rows of levels 1..lev; only the rows
+      // of the node's own level leave shared memory (the expansion reads a
+      // level-lev node's T only there, as the sibling's coupling term)
       const int rows = mv.koff[lev + 1];
+      const int own0 = mv.koff[lev];
       for (int w = threadIdx.x; w < nn * rows * RC; w += blockDim.x) {
         const int c = w % RC;
         const int e = (w / RC) % rows;
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
         const C* ch = cur + static_cast<size_t>(2 * t) * VS;
         const C v = ch[e * RC + c] + ch[VS + e * RC + c];
         nxt[static_cast<size_t>(t) * VS + e * RC + c] = v;
-        if (col0 + c < r) data[(static_cast<int64_t>(first + t) * r + col0 + c) * Ke + e] = v;
+        if (col0 + c < r && e >= own0) data[(static_cast<int64_t>(first + t) * r + col0 + c) * Ke + e] = v;
       }
     }
     __syncthreads();
@@ -679,7 +682,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 2) k_tree_cluster(MatView mv, Sc
           const int c = w % RC, e = w / RC;
           const C v = ch[e * RC + c] + ch[VS + e * RC + c];
           tx[e * RC + c] = v;
-          if (col0 + c < r) data[(static_cast<int64_t>(q) * r + col0 + c) * Ke + e] = v;
+          if (col0 + c < r && e >= mv.koff[lev]) data[(static_cast<int64_t>(q) * r + col0 + c) * Ke + e] = v;
         }
       }
     }
