@@ -874,7 +874,7 @@ def _run_exp(hm, torch, np, peaks, pipes, steps, warmup, with_cpu, storages=None
                 w = split_work(w, gen_counts(g), n, r, st)
             nst = max(3, steps // 2) if (st == "f64" and r > 1) else max(steps, 20)
             res, Y = time_variant(hm, torch, tree, g, st, X, nst, 2, 1, prof_steps=min(nst, 10))
-            ent = summarize(res, w, st, peaks, pipes, (st == "bf16" and r >= 4) or (st == "bf16x2" and r >= 16),
+            ent = summarize(res, w, st, peaks, pipes, st in ("bf16", "bf16x2") and r >= 16,
                             {"workload": "hodlr exp kernel n=262144 leaf=256 K=8 r=%d" % r, "storage": st,
                              "x_dtype": X_DTYPE[st],
                              "l2": "one matrix of %.0f MB per product (larger than L2)" % (res["generator_bytes"] / 1e6),

@@ -317,9 +317,8 @@ hm_status hm_selftest_device_timeout(void* stream);
 hm_status hm_inject_alloc_failures(int32_t count);
 
 /* Selects the kernel family for later products on this matrix:
- * 0 = automatic (tensor cores for BF16 storage from r = 4 and for BF16X2
- * from r = 16; SIMT kernels otherwise), 1 = SIMT only, 2 = tensor cores
- * whenever supported. */
+ * 0 = automatic (tensor cores when r is wide enough and storage is BF16 or
+ * BF16X2), 1 = SIMT only, 2 = tensor cores whenever supported. */
 hm_status hm_matrix_set_path(hm_matrix* A, int32_t path);
 
 /* Kernels for the tree phases of later products on this matrix (Sec. 4.1:

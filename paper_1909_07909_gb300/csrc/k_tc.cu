@@ -63,16 +63,10 @@ void make_tensor_maps(hm_matrix* A) {
   }
 }
 
-// Automatic choice: the tensor cores from 4 columns for BF16 and from 16 for
-// split BF16 (measured on the exponential-kernel workload, n = 262144: BF16
-// at r = 8 expands in 61 us on the tensor cores against 113 us in the SIMT
-// kernel, at r = 1-2 the SIMT kernel wins; split BF16 breaks even at r = 8).
-static int tensor_core_min_r(int storage) { return storage == HM_BF16 ? 4 : 16; }
-
 bool use_tensor_cores(const hm_matrix* A, int64_t r) {
   if (!A->tm_ok || A->path == 1) return false;
   if (A->storage != HM_BF16 && A->storage != HM_BF16X2) return false;
-  return A->path == 2 || r >= tensor_core_min_r(A->storage);
+  return A->path == 2 || r >= 16;
 }
 
 static size_t tc_smem(bool split, int NT, int nK, int nst, int mt = 1) {

@@ -66,12 +66,6 @@ class Bound(float):
     __radd__ = __add__
 
 
-def tensor_core_path(storage, r):
-    """Whether the library's automatic choice (hm_matrix_set_path 0) runs a
-    product of r columns on the tensor cores."""
-    return (storage == "bf16" and r >= 4) or (storage == "bf16x2" and r >= 16)
-
-
 def bound_factor(storage, kind, p, acc_len, tensor_core=False):
     """(c_round * u_s + gamma_L(u_acc)): rounded factors on the longest product chain
     (HODLR: U, V, X and the staged T; HSS: U, V, X, y-hat and the 2(p-1) translations

@@ -70,8 +70,7 @@ def test_reduced_precision_within_bound(kind, storage, xt, r):
     ref = OM.matmat(c, g, X)
     info = A.info()
     H.check_bound(Y, ref, OB.envelope(c, g, X),
-                  H.bound_factor(storage, kind, info["depth"], H.acc_length(info, kind),
-                                 tensor_core=H.tensor_core_path(storage, r)), storage)
+                  H.bound_factor(storage, kind, info["depth"], H.acc_length(info, kind)), storage)
 
 
 @pytest.mark.parametrize("kind", ["hodlr", "hss"])

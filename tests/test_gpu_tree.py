@@ -65,7 +65,7 @@ def test_cluster_tree_matches_level_kernels(storage, name, kind, c, k, r):
     assert np.array_equal(y_cluster, y_auto)
     ref = OM.matmat(c, g, X)
     info = A.info()
-    tc = H.tensor_core_path(storage, r)
+    tc = storage in ("bf16", "bf16x2") and r >= 16
     fac = H.bound_factor(storage, kind, info["depth"], H.acc_length(info, kind), tensor_core=tc)
     H.check_bound(y_cluster, ref, OB.envelope(c, g, X), fac, name)
     if storage == "f64":
