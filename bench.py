@@ -634,6 +634,12 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def run_batched(args):
+    print(json.dumps(batched_result(args)))
+    return 0
+
+
+def batched_result(args):
+    """The batched workload (one JSON object; args: steps, warmup, count)."""
     import numpy as np
     import torch
     import workloads as W
@@ -712,8 +718,7 @@ def run_batched(args):
     out["variants"] = res
     out["batched_vs_fp64_unbatched"] = res["bf16"]["batched_gbs"] / res["f64"]["loop_gbs"]
     out["gpu_launches"] = res["bf16"]["launches_per_run"] * args.steps
-    print(json.dumps(out))
-    return 0
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -722,6 +727,12 @@ def run_batched(args):
 # ---------------------------------------------------------------------------
 
 def run_serve(args):
+    print(json.dumps(serve_result(args)))
+    return 0
+
+
+def serve_result(args):
+    """The serving workload (one JSON object; args: count, rates, seconds)."""
     import numpy as np
     import torch
     import workloads as W
@@ -809,8 +820,33 @@ def run_serve(args):
            "by_rate": by_rate, "fp64_unbatched_ms_per_request_r8": f64_ms,
            "resident_bytes": server.stats()["resident_bytes"]}
     server.close()
-    print(json.dumps(out))
-    return 0
+    return out
+
+
+def batched_and_served(args, torch):
+    """Compact entries for the batched (512 matrices) and served (64 resident
+    matrices, Poisson arrivals) workloads, run after the single-matrix ones."""
+    import types
+    torch.cuda.empty_cache()
+    ns = types.SimpleNamespace(steps=max(3, min(10, args.steps)), warmup=2, count=0, rates=args.rates,
+                               seconds=min(args.seconds, 0.5))
+    b = batched_result(ns)
+    keep = ("batched_ms", "batched_gbs", "loop_ms", "loop_gbs", "launches_per_run", "bytes_per_run")
+    out = {"batched_512": {"value": b["value"], "unit": "GB/s", "ms_per_step": b["ms_per_step"],
+                           "config": b["config"]["workload"],
+                           "batched_vs_fp64_unbatched": b["batched_vs_fp64_unbatched"],
+                           "storages": {k: {f: v[f] for f in keep if f in v} for k, v in b["variants"].items()}}}
+    torch.cuda.empty_cache()
+    sv = serve_result(ns)
+    out["served_64"] = {"value": sv["value"], "unit": sv["unit"], "p50_ms": sv["ms_per_step"],
+                        "sustained_rps": sv["sustained_rps"],
+                        "saturation_throughput_rps": sv["saturation_throughput_rps"],
+                        "fp64_unbatched_ms_per_request_r8": sv["fp64_unbatched_ms_per_request_r8"],
+                        "config": sv["config"]["workload"],
+                        "by_rate": {k: {f: v[f] for f in ("p50_ms", "p99_ms", "throughput_rps", "refused")}
+                                    for k, v in sv["by_rate"].items()}}
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_workloads(hm, torch, np, peaks, pipes, steps, warmup, with_cpu, which=("hodlr4096", "exp"), storages=None,
@@ -1029,6 +1065,7 @@ def main():
             variants["ulv_solve_f64"] = time_ulv(hm, torch, tree, g, X, max(5, min(20, args.steps)))
         if not args.no_workloads:
             variants.update(run_workloads(hm, torch, np, peaks, pipes, args.steps, 3, not args.no_cpu and world == 1))
+            variants.update(batched_and_served(args, torch))
         if not args.no_cpu and world == 1:
             # the timed CPU baseline: the fast tree product on every host core
             secs, thr, Ycpu = cpu_fast_baseline(c, g, X)
