@@ -266,8 +266,10 @@ static hm_status launch_tcp_nt(hm_matrix* A, const MatView& mv, const Scratch& w
   const int ke = PROJ ? 0 : mv.Ke;
   const int mt = (tiles >= 2 && 2 * TPT <= 256) ? 2 : 1;
   if (2 * mt * TPT > 512) return HM_EUNSUPPORTED;
+  // rings of at least 3 stages only (a 2-stage ring is not used; the
+  // one-item-per-CTA kernel takes those shapes)
   int nst = TCP_MAX_STAGES;
-  while (nst > 2 && tcp_smem_bytes(NT, mt, nst, ke) > 227 * 1024) --nst;
+  while (nst > 3 && tcp_smem_bytes(NT, mt, nst, ke) > 227 * 1024) --nst;
   if (tcp_smem_bytes(NT, mt, nst, ke) > 227 * 1024) return HM_EUNSUPPORTED;
   // all of an SM's shared memory, whatever the ring needs: the CTA has its SM
   // to itself (no CTA of the neighbouring kernels, which programmatic launch
