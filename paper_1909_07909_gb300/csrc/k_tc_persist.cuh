@@ -58,9 +58,9 @@ __host__ __device__ inline size_t tcp_stage_bytes(int NT, int mt) {
 __host__ __device__ inline int tcp_ke4(int Ke) { return (Ke + 3) & ~3; }
 
 // Dynamic shared memory: 1024 bytes of alignment slack, the stages, the Z
-// block (NT columns of tcp_ke4(Ke) floats), 256 bytes of barriers and flags.
+// block (NT columns of tcp_ke4(Ke) floats), 512 bytes of barriers and flags.
 __host__ __device__ inline size_t tcp_smem_bytes(int NT, int mt, int nst, int Ke) {
-  return 1024 + static_cast<size_t>(nst) * tcp_stage_bytes(NT, mt) + static_cast<size_t>(NT) * tcp_ke4(Ke) * 4 + 256;
+  return 1024 + static_cast<size_t>(nst) * tcp_stage_bytes(NT, mt) + static_cast<size_t>(NT) * tcp_ke4(Ke) * 4 + 512;
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
   const uint32_t acce0 = accf0 + 16;                             // 2 barriers, every epilogue thread
   const uint32_t fin = acce0 + 16;                               // the MMA thread's last commit
   const uint32_t zbar = fin + 8;                                 // bulk copies of the Z block
+  const uint32_t bfree0 = full0 + 256;                           // nst barriers, producer: "B of this use is yours"
   uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 16 * TCP_MAX_STAGES + 48);    // after fin (bytes 160..167)
   volatile int* s_dead = reinterpret_cast<volatile int*>(tslot + 1);
   volatile int* s_flag = s_dead + 1;
@@ -271,6 +272,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     }
     mbar_init(fin, 1);
     mbar_init(zbar, 1);
+    for (int s = 0; s < nst; ++s) mbar_init(bfree0 + 8 * s, 1);
     *s_dead = 0;
     *s_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -306,6 +308,10 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
           if (c < nXt) {
             tma_load_2d(st + mt * A_BYTES, &tmX, static_cast<int>(w.a0) + c * TC_KC, w.col0, full0 + 8 * s);
             mbar_arrive1(full0 + 8 * s);                          // arrival 2: B comes with the copies
+          } else {
+            // the stagers write this use's B: the slot is free (the empty wait
+            // above) and its full barrier is in this use's phase
+            mbar_arrive1(bfree0 + 8 * s);
           }
           *s_issued = g + 1;
         }
@@ -358,6 +364,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
   } else if (warp < 4) {
     // ---- B chunks TMA does not bring ----
     const int stid = threadIdx.x - 64;
+    int bcount[TCP_MAX_STAGES] = {0, 0, 0, 0, 0, 0, 0, 0};       // uses of each slot the stagers filled
     bool waited = false;
     int g = 0;
     bool stop = false;
@@ -376,13 +383,18 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
       for (int c = 0; c < nK; ++c, ++g) {
         if (c < nXt) continue;
         const int s = g % nst;
-        const int u = g / nst;
         if (stid == 0) {
+          // The producer's signal for this use of the slot; its phase count is
+          // the stagers' own count of the slot's uses they fill.  Waiting on
+          // the empty barrier instead could run more than one phase ahead of
+          // it (the chunks TMA fills pass without the stagers), and a parity
+          // wait that far ahead returns at once.
           int ok = *s_dead ? 0 : 1;
-          if (ok && u > 0 && !mbar_wait(empty0 + 8 * s, (u - 1) & 1, err, 42)) {
+          if (ok && !mbar_wait(bfree0 + 8 * s, bcount[s] & 1, err, 42)) {
             ok = 0;
             *s_dead = 1;
           }
+          ++bcount[s];
           *s_flag = ok;
         }
         named_bar_sync(2, 64);
