@@ -270,8 +270,8 @@ hm_status hm_hss_matmat(const hm_matrix* A, int64_t r, const void* X, int64_t ld
  *     with HM_EINVAL and a message naming the limit; split the columns of X.
  *   - X and Y must be device memory (host buffers would need staging memory)
  *     and must not overlap (HM_EINVAL).
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture.
+ *   - The first call on a device looks up the array's device address (a
+ *     runtime query, no allocation).
  *   - Every call shares the array and it keeps the previous call's contents;
  *     the call clears what must start at zero on `stream`.  Calls whose
  *     kernels overlap on the GPU (concurrent streams or host threads) race on
