@@ -386,9 +386,10 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
         if (stid == 0) {
           // The producer's signal for this use of the slot; its phase count is
           // the stagers' own count of the slot's uses they fill.  Waiting on
-          // the empty barrier instead could run more than one phase ahead of
+          // the empty barrier instead could run two or more phases ahead of
           // it (the chunks TMA fills pass without the stagers), and a parity
-          // wait that far ahead returns at once.
+          // wait cannot tell a phase from the one two before it: it returned
+          // while the MMAs still read the slot.
           int ok = *s_dead ? 0 : 1;
           if (ok && !mbar_wait(bfree0 + 8 * s, bcount[s] & 1, err, 42)) {
             ok = 0;
