@@ -823,6 +823,18 @@ def serve_result(args):
     return out
 
 
+def guarded(variants, name, fn):
+    """Adds fn()'s entries to variants; an exception (a refused request, a
+    timed-out device wait) becomes {name: {"error": ...}} and a traceback on
+    stderr, so that the headline measured before it is still printed."""
+    try:
+        variants.update(fn())
+    except Exception as e:  # noqa: BLE001 - recorded in the output line, not swallowed
+        import traceback
+        traceback.print_exc()
+        variants[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+
+
 def batched_and_served(args, torch):
     """Compact entries for the batched (512 matrices) and served (64 resident
     matrices, Poisson arrivals) workloads, run after the single-matrix ones."""
@@ -1062,10 +1074,12 @@ def main():
                                     "phase_ms_per_step": {PHASES[k]: r_["phases"]["ms"][k] / r_["phases"]["steps"]
                                                           for k in range(len(PHASES))}}
         if not args.no_variants and not args.no_solve:
-            variants["ulv_solve_f64"] = time_ulv(hm, torch, tree, g, X, max(5, min(20, args.steps)))
+            guarded(variants, "ulv_solve_f64", lambda: {"ulv_solve_f64": time_ulv(hm, torch, tree, g, X,
+                                                                                 max(5, min(20, args.steps)))})
         if not args.no_workloads:
-            variants.update(run_workloads(hm, torch, np, peaks, pipes, args.steps, 3, not args.no_cpu and world == 1))
-            variants.update(batched_and_served(args, torch))
+            guarded(variants, "workloads", lambda: run_workloads(hm, torch, np, peaks, pipes, args.steps, 3,
+                                                                 not args.no_cpu and world == 1))
+            guarded(variants, "batched_and_served", lambda: batched_and_served(args, torch))
         if not args.no_cpu and world == 1:
             # the timed CPU baseline: the fast tree product on every host core
             secs, thr, Ycpu = cpu_fast_baseline(c, g, X)

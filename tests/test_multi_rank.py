@@ -77,3 +77,18 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
         steps = 1
         warmup = 0
     assert b.run_reference(A()) == 0                     # no work, exit code 0
+
+
+def test_guarded_variant_records_its_error():
+    """A failing secondary workload becomes an entry with its error; the
+    entries before it and the line's headline are kept."""
+    b = _bench()
+    variants = {"f32": {"value": 1.0}}
+    b.guarded(variants, "served", lambda: {"served_64": {"value": 2.0}})
+    assert variants["served_64"] == {"value": 2.0}
+
+    def fail():
+        raise RuntimeError("request refused")
+    b.guarded(variants, "workloads", fail)
+    assert variants["workloads"]["error"] == "RuntimeError: request refused"
+    assert variants["f32"] == {"value": 1.0}
